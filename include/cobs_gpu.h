@@ -1,0 +1,261 @@
+/*
+ * cobs_gpu.h -- C ABI of the GB300 (sm_103a) COBS query engine.
+ *
+ * COBS (Bingmann, Bradley, Gauger, Iqbal, "COBS: a Compact Bit-Sliced Signature
+ * Index", arXiv:1905.09624) indexes a list of documents by one Bloom filter per
+ * document, stored bit-sliced: row r of a block holds bit r of every filter of the
+ * block (Sec. 2.2).  A query hashes its distinct q-grams ("terms", Sec. 2.1),
+ * gathers h rows per term in every block, ANDs them, adds the resulting bits into
+ * per-document scores and reports the documents whose score is at least
+ * ceil(K * l), l = number of distinct query terms (Sec. 2.1, Sec. 2.2).  The
+ * compact layout sorts documents by size and gives every block of B documents its
+ * own Bloom size; one wide hash is reduced modulo each block's size (Sec. 2.2).
+ *
+ * Conventions for every call:
+ *   - Every call returns a cobs_status; nothing throws across the ABI.  On an error
+ *     cobs_last_error() returns a message (thread-local, valid until the next call
+ *     on the same thread).  Out-parameters are untouched on error.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global
+ *     memory on the index's device.  Input arrays are borrowed for the duration of
+ *     the call only (device inputs: until the work queued on the stream has run).
+ *   - Objects returned through `**out` are owned by the library and released by
+ *     their matching *_free call.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream); work is
+ *     queued on it.  Calls that return host results synchronise that stream.
+ *   - Term kinds: 0 = DNA canonical k-mer (min of the 2-bit code of the k-mer and
+ *     of its reverse complement, first base most significant, A=0 C=1 G=2 T=3),
+ *     1 = DNA forward k-mer, 2 = byte q-gram (q bytes read little-endian).  Windows
+ *     of DNA kinds that contain a byte other than 'A','C','G','T' are skipped
+ *     (Sec. 2.1 q-grams; Sec. 2.3 canonical k-mers).
+ *   - Hash i of a term t is XXH64 of the 8 little-endian bytes of t with seed i
+ *     (Sec. 2.3 names xxHash); its row in block b is that hash modulo w_b (Sec. 2.2).
+ */
+#ifndef COBS_GPU_H
+#define COBS_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    COBS_OK = 0,
+    COBS_PENDING = 1,        /* serve: the ticket's result is not ready yet */
+    COBS_ERR_ARG = -1,       /* invalid argument (message says which) */
+    COBS_ERR_OOM = -2,       /* a device or host allocation failed */
+    COBS_ERR_CUDA = -3,      /* a CUDA runtime call failed (message has the CUDA error) */
+    COBS_ERR_TIMEOUT = -4,   /* a bounded wait ran out */
+    COBS_ERR_BUDGET = -5,    /* serve: request can never fit the score-buffer budget */
+    COBS_ERR_FORMAT = -6,    /* index file is not a cobs_gpu index or is truncated */
+    COBS_ERR_OVERFLOW = -7,  /* a query has more terms than the score width can count */
+    COBS_ERR_NOT_FOUND = -8  /* serve: unknown or already released ticket */
+} cobs_status;
+
+/* Index parameters (Sec. 2.1-2.3). */
+typedef struct cobs_params {
+    uint32_t term_kind;   /* 0 DNA canonical, 1 DNA forward, 2 byte q-gram */
+    uint32_t q;           /* term length: 1..32 for DNA kinds, 1..8 for bytes */
+    uint32_t num_hashes;  /* h >= 1 hash functions per filter (Sec. 2.1 "k") */
+    uint32_t score_bits;  /* 16 or 32: width of the reported score counters */
+    double fpr;           /* target false-positive rate p of every filter, 0 < p < 1 */
+    uint64_t block_docs;  /* B documents per block (compact); 0 = classic, one block in input order */
+} cobs_params;
+
+/* One block of the index; same meaning on host and device.  Sec. 2.2: documents at
+ * sorted positions [doc_begin, doc_begin + n_docs) share one Bloom size w, stored
+ * as w rows of rowbytes bytes; document j of the block is bit (j & 7) of byte
+ * (j >> 3) of each row; padding bits are zero. */
+typedef struct cobs_block_info {
+    uint64_t n_docs;      /* documents in the block */
+    uint64_t doc_begin;   /* first sorted position */
+    uint64_t w;           /* Bloom filter size = rows; w = max(1, ceil(-h V / ln(1 - p^(1/h)))) */
+    uint64_t rowbytes;    /* ceil(n_docs / 128) * 16 */
+    uint64_t row_offset;  /* byte offset of the block's row 0 in the row storage */
+    uint64_t max_terms;   /* V: largest distinct-term count of a document in the block */
+} cobs_block_info;
+
+typedef struct cobs_index cobs_index;               /* host copy of an index */
+typedef struct cobs_device_index cobs_device_index; /* index resident in device memory */
+typedef struct cobs_engine cobs_engine;             /* query workspace bound to a device index */
+typedef struct cobs_server cobs_server;             /* continuous-batching serve loop */
+
+/* Per-query result: hits sorted by score descending, then document id ascending. */
+typedef struct cobs_hits {
+    uint32_t n_terms;     /* l = distinct terms of the query; 0 => no hits */
+    uint32_t min_score;   /* ceil(K * l), K in permille: (K * l + 999) / 1000 */
+    uint32_t n_hits;
+    uint32_t _pad;
+    const uint32_t *doc_ids;  /* original document ids (input order of the build) */
+    const uint32_t *scores;   /* score of each hit (number of terms present) */
+} cobs_hits;
+
+typedef struct cobs_result {
+    uint64_t n_queries;
+    const cobs_hits *hits;    /* hits[i] for query i; storage owned by the result */
+} cobs_result;
+
+/* Query forms (flags of cobs_query_batch / cobs_engine_query*). */
+#define COBS_PLAIN   1u  /* one query per kernel sequence, queries one after another */
+#define COBS_BATCHED 2u  /* all queries in one persistent launch (row slices shared through L2) */
+#define COBS_GRAPH   4u  /* COBS_BATCHED, replayed from a captured CUDA graph */
+
+/* ------------------------------------------------------------------ build */
+
+/* Build an index on the device from host documents (Sec. 2.3 "Classic and
+ * Compact").  docs: all documents concatenated (host); doc_offsets: n_docs + 1
+ * host offsets, document d = docs[doc_offsets[d] .. doc_offsets[d+1]).
+ * Steps on the device: distinct-term count per document, host planning (sort by
+ * (count, id) for compact, Bloom size per block), Bloom bit-setting into the
+ * row-major blocks.  n_docs may be 0.  Errors: ARG (bad params, w_b >= 2^32,
+ * n_docs >= 2^32), OOM, CUDA. */
+cobs_status cobs_build_device(const cobs_params *params, const uint8_t *docs, const uint64_t *doc_offsets,
+                              uint64_t n_docs, int device, void *stream, cobs_device_index **out);
+
+/* Same as cobs_build_device, but docs and doc_offsets are DEVICE pointers on the
+ * current device, already resident; doc_offsets_host is a host copy of the offsets
+ * (used to plan the work; must equal the device array). */
+cobs_status cobs_build_device_resident(const cobs_params *params, const uint8_t *docs_dev,
+                                       const uint64_t *doc_offsets_dev, const uint64_t *doc_offsets_host,
+                                       uint64_t n_docs, void *stream, cobs_device_index **out);
+
+/* Build on the device and return a host copy (cobs_build_device + download). */
+cobs_status cobs_build(const cobs_params *params, const uint8_t *docs, const uint64_t *doc_offsets,
+                       uint64_t n_docs, cobs_index **out);
+
+/* Copy a device index to the host (bit-exact: blocks, permutation, rows). */
+cobs_status cobs_device_index_download(const cobs_device_index *dix, cobs_index **out);
+
+/* Upload a host index to `device`; the index stays resident until freed. */
+cobs_status cobs_load_device(const cobs_index *ix, int device, void *stream, cobs_device_index **out);
+
+/* Save / load the library's own file format (header, block table, permutation,
+ * per-document term counts, rows; little-endian).  load: FORMAT on a bad file. */
+cobs_status cobs_index_save(const cobs_index *ix, const char *path);
+cobs_status cobs_index_load(const char *path, cobs_index **out);
+
+/* Inspect a host index.  Pointers stay valid until cobs_index_free.
+ * perm[i] = original id of the document at sorted position i;
+ * nterms[d] = distinct terms of original document d. */
+cobs_status cobs_index_info(const cobs_index *ix, cobs_params *params, uint64_t *n_docs, uint64_t *n_blocks,
+                            const cobs_block_info **blocks, const uint64_t **perm, const uint64_t **nterms,
+                            const uint8_t **rows, uint64_t *rows_bytes);
+
+/* Inspect a device index (host copies of the table; device pointer to the rows). */
+cobs_status cobs_device_index_info(const cobs_device_index *dix, cobs_params *params, uint64_t *n_docs,
+                                   uint64_t *n_blocks, const cobs_block_info **blocks,
+                                   const void **rows_dev, uint64_t *rows_bytes);
+
+void cobs_index_free(cobs_index *ix);
+void cobs_device_index_free(cobs_device_index *dix);
+
+/* ------------------------------------------------------------------ query */
+
+/* Query a device index from HOST buffers: copies the queries to the device, runs
+ * the query path (Sec. 2.2: terms, hash, AND of h rows, ADD into scores,
+ * threshold), copies the hits back.  queries: all queries concatenated;
+ * query_offsets: n + 1 offsets; threshold_permille[i] in 1..1000 is K of query i.
+ * flags: one of COBS_PLAIN, COBS_BATCHED, COBS_GRAPH.  Results are identical for
+ * every flag.  Errors: ARG (threshold 0 or > 1000, bad flags), OVERFLOW (a query
+ * has more than 2^score_bits - 1 windows), OOM, CUDA. */
+cobs_status cobs_query_batch(cobs_device_index *dix, const uint8_t *queries, const uint64_t *query_offsets,
+                             const uint16_t *threshold_permille, uint64_t n, uint32_t flags, void *stream,
+                             cobs_result **out);
+void cobs_result_free(cobs_result *res);
+
+/* Engine: a reusable workspace for repeated query batches on one device index.
+ * max_queries / max_query_bytes size the initial buffers (they grow on demand,
+ * except inside a captured graph).  The engine queues all work on `stream`. */
+typedef struct cobs_engine_cfg {
+    uint64_t max_queries;
+    uint64_t max_query_bytes;
+    uint64_t max_hits;        /* initial hit capacity (0 = 1M); grows and re-runs on overflow */
+    uint32_t slice_bytes;     /* batched row-slice width: 32, 64 or 128; 0 = autotune */
+    uint32_t ctas_per_sm;     /* persistent grid = SMs * ctas_per_sm; 0 = autotune */
+} cobs_engine_cfg;
+
+cobs_status cobs_engine_create(cobs_device_index *dix, const cobs_engine_cfg *cfg, void *stream,
+                               cobs_engine **out);
+void cobs_engine_free(cobs_engine *eng);
+
+/* Query from DEVICE-resident inputs (bytes, offsets, thresholds on the device);
+ * offsets_host is a host copy of the offsets used to plan tiles (must equal the
+ * device array).  Asynchronous: results stay on the device (see
+ * cobs_engine_results_device) and are complete when the engine stream reaches
+ * this point. */
+cobs_status cobs_engine_query_device(cobs_engine *eng, const uint8_t *queries_dev, const uint64_t *offsets_dev,
+                                     const uint64_t *offsets_host, const uint16_t *thr_dev, uint64_t n,
+                                     uint32_t flags);
+
+/* Query from HOST inputs through the engine (H2D, query, D2H; synchronises). */
+cobs_status cobs_engine_query_host(cobs_engine *eng, const uint8_t *queries, const uint64_t *offsets,
+                                   const uint16_t *thr, uint64_t n, uint32_t flags, cobs_result **out);
+
+/* Device pointers to the last query's results (valid until the next query):
+ * n_terms[n], min_score[n], hit_offsets[n+1] (u64), hit_ids[total], hit_scores[total]. */
+cobs_status cobs_engine_results_device(cobs_engine *eng, const uint32_t **n_terms, const uint32_t **min_score,
+                                       const uint64_t **hit_offsets, const uint32_t **hit_ids,
+                                       const uint32_t **hit_scores);
+
+/* Copy the last query's results to the host (synchronises the engine stream). */
+cobs_status cobs_engine_download(cobs_engine *eng, cobs_result **out);
+
+/* Timing of the last query's kernels, measured with CUDA events on the engine
+ * stream: ms of the term kernel, the gather/AND/ADD kernel(s), the hit kernels,
+ * and the whole sequence; plus algorithmic row bytes gathered (h * rowbytes_b per
+ * term and block) and distinct terms.  Synchronises the engine stream. */
+typedef struct cobs_query_stats {
+    double ms_terms, ms_gather, ms_hits, ms_total;
+    uint64_t row_bytes, terms, n_tiles, gather_launches, launches;
+    uint32_t slice_bytes, ctas_per_sm;
+} cobs_query_stats;
+cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out);
+
+/* Autotune the batched kernel's slice width and grid on a sample batch (device
+ * inputs as in cobs_engine_query_device); the choice is kept by the engine and
+ * cached per index shape.  Writes the chosen values to cfg_out. */
+cobs_status cobs_engine_autotune(cobs_engine *eng, const uint8_t *queries_dev, const uint64_t *offsets_dev,
+                                 const uint64_t *offsets_host, const uint16_t *thr_dev, uint64_t n,
+                                 cobs_engine_cfg *cfg_out);
+
+/* ------------------------------------------------------------------ serve */
+
+typedef struct cobs_serve_cfg {
+    uint64_t score_budget_bytes; /* admission budget for in-flight work (0 = 4 GiB) */
+    uint32_t max_inflight_waves; /* waves on the device at once (0 = 2) */
+    uint32_t max_wave_queries;   /* queries per wave (0 = 4096) */
+    uint32_t wait_timeout_ms;    /* bounded waits for completions (0 = 10000) */
+    uint32_t _pad;
+} cobs_serve_cfg;
+
+typedef struct cobs_serve_stats {
+    uint64_t completed, waves, rejected;
+    double p50_ms, p99_ms, max_ms, qps, seconds;
+} cobs_serve_stats;
+
+/* Start a serve loop on a device index (one scheduler thread; waves overlap on the
+ * device on separate streams).  submit copies the query; poll returns COBS_PENDING
+ * until the result is ready, then fills *out (valid until cobs_hits_release).
+ * submit returns BUDGET if the query can never be admitted. */
+cobs_status cobs_serve_start(cobs_device_index *dix, const cobs_serve_cfg *cfg, cobs_server **out);
+cobs_status cobs_serve_submit(cobs_server *srv, const uint8_t *q, uint64_t len, uint16_t thr_permille,
+                              uint64_t *ticket);
+cobs_status cobs_serve_poll(cobs_server *srv, uint64_t ticket, cobs_hits *out);
+void cobs_hits_release(cobs_server *srv, uint64_t ticket);
+cobs_status cobs_serve_stop(cobs_server *srv, cobs_serve_stats *out);
+
+/* --------------------------------------------------------------- misc */
+
+const char *cobs_last_error(void);
+
+/* Bloom size used by the planner: max(1, ceil(-h * v / ln(1 - p^(1/h)))), the
+ * Sec. 2.1 bound (1 - e^{-hv/w})^h = p solved for w at fixed h. */
+uint64_t cobs_bloom_width(uint32_t h, uint64_t v, double p);
+
+/* Library version string. */
+const char *cobs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COBS_GPU_H */

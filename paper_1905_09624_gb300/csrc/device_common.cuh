@@ -1,0 +1,130 @@
+// Device helpers shared by the COBS kernels: term codes, XXH64 of one 8-byte
+// term, Barrett reduction, device-side block table.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cobs {
+
+// Term kinds (Sec. 2.1 q-grams, Sec. 2.3 canonical k-mers).
+enum : uint32_t { KIND_DNA_CANONICAL = 0, KIND_DNA_FORWARD = 1, KIND_BYTES = 2 };
+
+// Device copy of one block (Sec. 2.2 compact layout): rows of `rowbytes` bytes,
+// w rows, documents [doc_begin, doc_begin + n_docs) in sorted order.
+struct DevBlock {
+    uint64_t row_offset;  // byte offset of row 0
+    uint64_t barrett_m;   // floor(2^64 / w) (UINT64_MAX for w == 1)
+    uint32_t w;
+    uint32_t rowbytes;
+    uint32_t n_docs;
+    uint32_t doc_begin;
+};
+
+// ---------------------------------------------------------------- XXH64
+// XXH64 of the 8 little-endian bytes of `v` with `seed`: the xxHash64 algorithm
+// for an input shorter than 32 bytes holding exactly one 8-byte lane (xxHash
+// specification: init with seed + PRIME5 + length, one lane round, avalanche).
+__device__ __forceinline__ uint64_t rotl64(uint64_t x, int r) { return (x << r) | (x >> (64 - r)); }
+
+__device__ __forceinline__ uint64_t xxh64_u64(uint64_t v, uint64_t seed) {
+    const uint64_t PR1 = 0x9E3779B185EBCA87ULL;
+    const uint64_t PR2 = 0xC2B2AE3D27D4EB4FULL;
+    const uint64_t PR3 = 0x165667B19E3779F9ULL;
+    const uint64_t PR4 = 0x85EBCA77C2B2AE63ULL;
+    const uint64_t PR5 = 0x27D4EB2F165667C5ULL;
+    uint64_t acc = seed + PR5 + 8ULL;
+    uint64_t lane = rotl64(v * PR2, 31) * PR1;
+    acc ^= lane;
+    acc = rotl64(acc, 27) * PR1 + PR4;
+    acc ^= acc >> 33;
+    acc *= PR2;
+    acc ^= acc >> 29;
+    acc *= PR3;
+    acc ^= acc >> 32;
+    return acc;
+}
+
+// ------------------------------------------------------------- Barrett
+// x mod w by Barrett reduction (P. Barrett, "Implementing the Rivest Shamir and
+// Adleman public key encryption algorithm on a standard digital signal processor",
+// CRYPTO 1986) with m = floor(2^64 / w): the quotient estimate
+// floor(x * m / 2^64) is at most one below floor(x / w), so one conditional
+// subtraction finishes.  Used for "one wide hash, then modulo each filter size"
+// (Sec. 2.2).
+__device__ __forceinline__ uint32_t barrett_mod(uint64_t x, uint64_t m, uint32_t w) {
+    uint64_t q = __umul64hi(x, m);
+    uint64_t r = x - q * (uint64_t)w;
+    return (uint32_t)(r >= w ? r - w : r);
+}
+
+// 2-bit code of a DNA byte: A=0 C=1 G=2 T=3, 4 = not a base.
+__device__ __forceinline__ uint32_t base2(uint8_t c) {
+    switch (c) {
+        case 'A': return 0u;
+        case 'C': return 1u;
+        case 'G': return 2u;
+        case 'T': return 3u;
+        default: return 4u;
+    }
+}
+
+__device__ __forceinline__ uint64_t kmer_mask(uint32_t k) { return k >= 32 ? ~0ULL : ((1ULL << (2 * k)) - 1ULL); }
+
+// Rolling window state for one thread walking positions left to right.
+// fwd: forward code of the last k bases (first base most significant);
+// rc: code of their reverse complement; run: consecutive valid bases seen.
+struct Roller {
+    uint64_t fwd, rc, bytes;
+    uint32_t run;
+};
+
+__device__ __forceinline__ void roll_init(Roller &r) { r.fwd = 0; r.rc = 0; r.bytes = 0; r.run = 0; }
+
+// Push byte c; returns true when the window of length k ending at c is a term,
+// and writes its code to *code.
+__device__ __forceinline__ bool roll_push(Roller &r, uint8_t c, uint32_t kind, uint32_t k, uint64_t mask,
+                                          uint64_t *code) {
+    if (kind == KIND_BYTES) {
+        // q bytes little-endian: the newest byte is the most significant of the window.
+        r.bytes = (r.bytes >> 8) | ((uint64_t)c << 56);
+        r.run = r.run < k ? r.run + 1 : k;
+        if (r.run < k) return false;
+        *code = k >= 8 ? r.bytes : (r.bytes >> (64 - 8 * k));
+        return true;
+    }
+    uint32_t b = base2(c);
+    if (b > 3u) { r.run = 0; return false; }
+    r.fwd = ((r.fwd << 2) | b) & mask;
+    // complement enters at the most significant end of the reverse complement
+    r.rc = (r.rc >> 2) | ((uint64_t)(3u - b) << (2 * (k - 1)));
+    r.run = r.run < k ? r.run + 1 : k;
+    if (r.run < k) return false;
+    *code = (kind == KIND_DNA_CANONICAL && r.rc < r.fwd) ? r.rc : r.fwd;
+    return true;
+}
+
+// Open-addressing set of 64-bit codes; EMPTY marks a free slot.  The value
+// EMPTY itself (possible only for 8-byte q-grams of 0xFF bytes) is tracked by a
+// separate flag by the caller.
+constexpr uint64_t EMPTY_KEY = 0xFFFFFFFFFFFFFFFFULL;
+
+// Insert `key` into the table of `cap` slots, first probe from hash `h` by
+// multiply-shift range reduction (Lemire, "Fast random integer generation in an
+// interval", 2019), then linear probing.  Returns true when this call inserted it
+// (first occurrence).  Every probe sequence ends: callers size the table at least
+// twice the number of insertions, so a free slot always exists.
+__device__ __forceinline__ bool set_insert(unsigned long long *table, uint32_t cap, uint64_t h, uint64_t key) {
+    uint32_t slot = (uint32_t)(((h >> 32) * (uint64_t)cap) >> 32);
+    for (uint32_t probe = 0; probe < cap; probe++) {
+        unsigned long long old = atomicCAS(&table[slot], (unsigned long long)EMPTY_KEY, (unsigned long long)key);
+        if (old == EMPTY_KEY) return true;
+        if (old == key) return false;
+        slot = slot + 1u == cap ? 0u : slot + 1u;
+    }
+    return false;  // unreachable for a correctly sized table
+}
+
+// Slots of the distinct-term set for `npos` windows.
+__host__ __device__ __forceinline__ uint64_t set_slots(uint64_t npos) { return npos * 2 < 16 ? 16 : npos * 2; }
+
+}  // namespace cobs

@@ -1,0 +1,334 @@
+// K2/K4: gather the h rows of every query term in a block, AND them, ADD the
+// indicator bits into per-document scores (Sec. 2.2), threshold (Sec. 2.1).
+//
+// Counters are bit-sliced ("vertical"): a lane owns 128 documents (one 16-byte
+// column of a row) and keeps, for each of its four 32-document words, L words
+// lv[0..L-1] such that the score of document bit j is sum_l bit_j(lv[l]) 2^l.
+// Indicator words are added 16 (or 8) at a time by a carry-save adder tree
+// (Harley and Seal's population-count scheme: each full adder is two 3-input
+// logic operations), the carry out of the tree is rippled into the upper levels.
+// This replaces the paper's byte-lookup expansion into 16-bit counters with SIMD
+// adds (Sec. 2.3), which needs about one add per 8 documents; the adder tree
+// needs about three logic operations per 32 documents.
+#include "kernels.cuh"
+
+namespace cobs {
+
+constexpr uint32_t FULL = 0xffffffffu;
+constexpr int GATHER_THREADS = 128;
+
+__device__ __forceinline__ void csa(uint32_t &hi, uint32_t &lo, uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t u = a ^ b;
+    hi = (a & b) | (u & c);
+    lo = u ^ c;
+}
+
+// Add G indicator words (G = 16 or 8) into the vertical counter lv[0..L-1].
+template <int L, int G>
+__device__ __forceinline__ void hs_add(uint32_t (&lv)[L], const uint32_t (&x)[G]) {
+    static_assert(G == 16 || G == 8, "group of 8 or 16");
+    if constexpr (G == 16) {
+        uint32_t twosA, twosB, foursA, foursB, eightsA, eightsB, sixteens;
+        csa(twosA, lv[0], lv[0], x[0], x[1]);
+        csa(twosB, lv[0], lv[0], x[2], x[3]);
+        csa(foursA, lv[1], lv[1], twosA, twosB);
+        csa(twosA, lv[0], lv[0], x[4], x[5]);
+        csa(twosB, lv[0], lv[0], x[6], x[7]);
+        csa(foursB, lv[1], lv[1], twosA, twosB);
+        csa(eightsA, lv[2], lv[2], foursA, foursB);
+        csa(twosA, lv[0], lv[0], x[8], x[9]);
+        csa(twosB, lv[0], lv[0], x[10], x[11]);
+        csa(foursA, lv[1], lv[1], twosA, twosB);
+        csa(twosA, lv[0], lv[0], x[12], x[13]);
+        csa(twosB, lv[0], lv[0], x[14], x[15]);
+        csa(foursB, lv[1], lv[1], twosA, twosB);
+        csa(eightsB, lv[2], lv[2], foursA, foursB);
+        csa(sixteens, lv[3], lv[3], eightsA, eightsB);
+        uint32_t c = sixteens;
+#pragma unroll
+        for (int l = 4; l < L; l++) {
+            uint32_t t = lv[l] & c;
+            lv[l] ^= c;
+            c = t;
+        }
+    } else {
+        uint32_t twosA, twosB, foursA, foursB, eights;
+        csa(twosA, lv[0], lv[0], x[0], x[1]);
+        csa(twosB, lv[0], lv[0], x[2], x[3]);
+        csa(foursA, lv[1], lv[1], twosA, twosB);
+        csa(twosA, lv[0], lv[0], x[4], x[5]);
+        csa(twosB, lv[0], lv[0], x[6], x[7]);
+        csa(foursB, lv[1], lv[1], twosA, twosB);
+        csa(eights, lv[2], lv[2], foursA, foursB);
+        uint32_t c = eights;
+#pragma unroll
+        for (int l = 3; l < L; l++) {
+            uint32_t t = lv[l] & c;
+            lv[l] ^= c;
+            c = t;
+        }
+    }
+}
+
+// Bit mask of the documents whose vertical count is >= mn (mn < 2^L).
+template <int L>
+__device__ __forceinline__ uint32_t ge_mask(const uint32_t (&lv)[L], uint32_t mn) {
+    uint32_t gt = 0u, eq = FULL;
+#pragma unroll
+    for (int l = L - 1; l >= 0; l--) {
+        uint32_t mb = ((mn >> l) & 1u) ? FULL : 0u;
+        gt |= eq & lv[l] & ~mb;
+        eq &= ~(lv[l] ^ mb);
+    }
+    return gt | eq;
+}
+
+template <int L>
+__device__ __forceinline__ uint32_t count_of(const uint32_t (&lv)[L], uint32_t bit) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int l = 0; l < L; l++) s |= ((lv[l] >> bit) & 1u) << l;
+    return s;
+}
+
+__device__ __forceinline__ uint4 ld_row(const uint8_t *p) {
+    return __ldcg(reinterpret_cast<const uint4 *>(p));
+}
+
+// Accumulate the terms [t0, t1) of one query for one 16-byte column.
+// ridx: row indices of hash 0 for this (query, block); hash i at + i * tcap.
+template <int L, int G>
+__device__ __forceinline__ void accumulate(uint32_t (&lv)[4][L], const uint8_t *colbase, uint32_t rowbytes,
+                                           const uint32_t *ridx, uint64_t tcap, uint32_t h, uint32_t t0,
+                                           uint32_t t1) {
+    for (uint32_t t = t0; t < t1; t += G) {
+        uint32_t x[4][G];
+        uint32_t row[G];
+#pragma unroll
+        for (int j = 0; j < G; j += 4) {
+            uint4 r = __ldg(reinterpret_cast<const uint4 *>(ridx + t + j));
+            row[j] = r.x; row[j + 1] = r.y; row[j + 2] = r.z; row[j + 3] = r.w;
+        }
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (t + j < t1) v = ld_row(colbase + (uint64_t)row[j] * rowbytes);
+            x[0][j] = v.x; x[1][j] = v.y; x[2][j] = v.z; x[3][j] = v.w;
+        }
+        for (uint32_t i = 1; i < h; i++) {
+            const uint32_t *ri = ridx + (uint64_t)i * tcap;
+#pragma unroll
+            for (int j = 0; j < G; j += 4) {
+                uint4 r = __ldg(reinterpret_cast<const uint4 *>(ri + t + j));
+                row[j] = r.x; row[j + 1] = r.y; row[j + 2] = r.z; row[j + 3] = r.w;
+            }
+#pragma unroll
+            for (int j = 0; j < G; j++) {
+                if (t + j < t1) {
+                    uint4 v = ld_row(colbase + (uint64_t)row[j] * rowbytes);
+                    x[0][j] &= v.x; x[1][j] &= v.y; x[2][j] &= v.z; x[3][j] &= v.w;
+                }
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < 4; w++) hs_add<L, G>(lv[w], x[w]);
+    }
+}
+
+// One warp-tile: QPW queries x one row slice of one block.
+template <int LPQ, int G, int L>
+__device__ __forceinline__ void tile_body(const GatherArgs &a, const DevBlock &blk, uint32_t block_idx,
+                                          uint32_t col, bool active, uint32_t q, uint32_t ell) {
+    uint32_t lv[4][L];
+#pragma unroll
+    for (int w = 0; w < 4; w++)
+#pragma unroll
+        for (int l = 0; l < L; l++) lv[w][l] = 0u;
+    const uint32_t n = active ? ell : 0u;
+    const uint32_t *ridx = a.rows_idx + (uint64_t)(block_idx * a.h) * a.tcap + a.term_base[q];
+    const uint8_t *colbase = a.rows + blk.row_offset + col;
+    accumulate<L, G>(lv, colbase, blk.rowbytes, ridx, a.tcap, a.h, 0u, n);
+    if (n == 0u) return;
+    const uint32_t mn = (uint32_t)(((uint64_t)a.thr[q] * ell + 999u) / 1000u);
+    const uint32_t doc0 = col * 8u;
+    uint32_t ge[4];
+    uint32_t nh = 0;
+#pragma unroll
+    for (int w = 0; w < 4; w++) {
+        uint32_t m = ge_mask<L>(lv[w], mn);
+        uint32_t jw = doc0 + 32u * w;
+        if (jw >= blk.n_docs) m = 0u;
+        else if (blk.n_docs - jw < 32u) m &= (1u << (blk.n_docs - jw)) - 1u;
+        ge[w] = m;
+        nh += __popc(m);
+    }
+    if (nh == 0u) return;
+    unsigned long long pos = atomicAdd(a.hit_count, (unsigned long long)nh);
+    atomicAdd(&a.qcount[q], nh);
+#pragma unroll
+    for (int w = 0; w < 4; w++) {
+        uint32_t m = ge[w];
+        while (m) {
+            uint32_t bit = __ffs(m) - 1u;
+            m &= m - 1u;
+            uint32_t score = count_of<L>(lv[w], bit);
+            uint32_t id = a.perm[blk.doc_begin + doc0 + 32u * w + bit];
+            if (pos < a.hit_cap) {
+                a.raw_q[pos] = q;
+                a.raw_key[pos] = ((unsigned long long)(~score) << 32) | id;
+            }
+            pos++;
+        }
+    }
+}
+
+// Persistent batched kernel.  Tiles are (row slice, group of QPW queries), slice
+// major, so the CTAs resident at any moment read the same few slices and the
+// slices stay in L2; within a slice the groups run longest query first.
+template <int LPQ, int G, int L>
+__global__ void __launch_bounds__(GATHER_THREADS) k_gather_batched(GatherArgs a) {
+    constexpr uint32_t QPW = 32 / LPQ;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t qslot = lane / LPQ;
+    const uint32_t c = lane % LPQ;
+    const unsigned long long n_tiles = (unsigned long long)a.n_slices * a.n_groups;
+    for (;;) {
+        unsigned long long tile = 0;
+        if (lane == 0) tile = atomicAdd(a.work_counter, 1ULL);
+        tile = __shfl_sync(FULL, tile, 0);
+        if (tile >= n_tiles) break;
+        const uint32_t s = (uint32_t)(tile / a.n_groups);
+        const uint32_t g = (uint32_t)(tile % a.n_groups);
+        const SliceDesc sd = a.slices[s];
+        const DevBlock blk = a.blocks[sd.block];
+        const uint32_t qi = g * QPW + qslot;
+        const bool valid = qi < a.n_queries;
+        const uint32_t q = valid ? a.order[qi] : 0u;
+        const uint32_t ell = valid ? a.ell[q] : 0u;
+        const uint32_t col = sd.byte_off + c * 16u;
+        const bool active = valid && col < blk.rowbytes;
+        tile_body<LPQ, G, L>(a, blk, sd.block, col, active, q, ell);
+    }
+}
+
+template <int LPQ, int G>
+static void launch_L(const GatherArgs &a, uint32_t L, uint32_t grid, cudaStream_t s) {
+    switch (L) {
+        case 8: k_gather_batched<LPQ, G, 8><<<grid, GATHER_THREADS, 0, s>>>(a); break;
+        case 12: k_gather_batched<LPQ, G, 12><<<grid, GATHER_THREADS, 0, s>>>(a); break;
+        case 16: k_gather_batched<LPQ, G, 16><<<grid, GATHER_THREADS, 0, s>>>(a); break;
+        default: k_gather_batched<LPQ, G, 24><<<grid, GATHER_THREADS, 0, s>>>(a); break;
+    }
+}
+
+uint32_t counter_levels_for(uint32_t max_terms) {
+    uint32_t bits = 0;
+    while (bits < 32 && (max_terms >> bits)) bits++;
+    if (bits <= 8) return 8;
+    if (bits <= 12) return 12;
+    if (bits <= 16) return 16;
+    return 24;
+}
+
+void launch_gather_batched_L(const GatherArgs &a, uint32_t lanes_per_query, uint32_t L, uint32_t grid,
+                             cudaStream_t s) {
+    const bool g16 = a.h == 1;
+    switch (lanes_per_query) {
+        case 2: g16 ? launch_L<2, 16>(a, L, grid, s) : launch_L<2, 8>(a, L, grid, s); break;
+        case 4: g16 ? launch_L<4, 16>(a, L, grid, s) : launch_L<4, 8>(a, L, grid, s); break;
+        default: g16 ? launch_L<8, 16>(a, L, grid, s) : launch_L<8, 8>(a, L, grid, s); break;
+    }
+}
+
+int gather_batched_max_blocks_per_sm(uint32_t lanes_per_query, uint32_t h) {
+    int nb = 0;
+    if (h == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gather_batched<8, 16, 12>, GATHER_THREADS, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gather_batched<8, 8, 12>, GATHER_THREADS, 0);
+    (void)lanes_per_query;
+    return nb;
+}
+
+// ------------------------------------------------------------------ plain
+// One query: thread = (16-byte column over all blocks, chunk of PLAIN_CHUNK terms);
+// partial counts of a chunk are added to the score array with atomics.
+template <int G>
+__global__ void __launch_bounds__(PLAIN_THREADS) k_gather_plain(PlainArgs a) {
+    const uint32_t x = blockIdx.y * blockDim.x + threadIdx.x;
+    const uint32_t ell = a.ell[a.q];
+    const uint32_t t0 = blockIdx.x * PLAIN_CHUNK;
+    if (x >= a.n_cols || t0 >= ell) return;
+    const uint32_t t1 = t0 + PLAIN_CHUNK < ell ? t0 + PLAIN_CHUNK : ell;
+    const uint32_t b = a.col_block[x];
+    const uint32_t col = a.col_byte[x];
+    const DevBlock blk = a.blocks[b];
+    constexpr int L = 8;  // a chunk counts at most 128
+    uint32_t lv[4][L];
+#pragma unroll
+    for (int w = 0; w < 4; w++)
+#pragma unroll
+        for (int l = 0; l < L; l++) lv[w][l] = 0u;
+    const uint32_t *ridx = a.rows_idx + (uint64_t)(b * a.h) * a.tcap + a.term_base[a.q];
+    accumulate<L, G>(lv, a.rows + blk.row_offset + col, blk.rowbytes, ridx, a.tcap, a.h, t0, t1);
+    const uint32_t doc0 = col * 8u;
+#pragma unroll
+    for (int w = 0; w < 4; w++) {
+        uint32_t any = 0;
+#pragma unroll
+        for (int l = 0; l < L; l++) any |= lv[w][l];
+        while (any) {
+            uint32_t bit = __ffs(any) - 1u;
+            any &= any - 1u;
+            uint32_t j = doc0 + 32u * w + bit;
+            if (j < blk.n_docs) atomicAdd(&a.scores[blk.doc_begin + j], count_of<L>(lv[w], bit));
+        }
+    }
+}
+
+void launch_gather_plain(const PlainArgs &a, uint32_t n_chunks, cudaStream_t s) {
+    if (n_chunks == 0 || a.n_cols == 0) return;
+    // x: term chunks (up to 2^31 - 1), y: column groups (n_cols / 128 stays far below 65536)
+    dim3 grid(n_chunks, (a.n_cols + PLAIN_THREADS - 1) / PLAIN_THREADS);
+    if (a.h == 1) k_gather_plain<16><<<grid, PLAIN_THREADS, 0, s>>>(a);
+    else k_gather_plain<8><<<grid, PLAIN_THREADS, 0, s>>>(a);
+}
+
+// Threshold of the plain form: scan the score array, compact the hits with a
+// warp ballot and one atomic per warp.
+__global__ void k_plain_threshold(ThresholdArgs a) {
+    const uint32_t ell = a.ell[a.q];
+    if (ell == 0u) return;
+    const uint32_t mn = (uint32_t)(((uint64_t)a.thr[a.q] * ell + 999u) / 1000u);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t iters = (a.n_docs + stride - 1) / stride;
+    for (uint32_t it = 0; it < iters; it++) {
+        uint32_t p = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        uint32_t sc = p < a.n_docs ? a.scores[p] : 0u;
+        bool hit = p < a.n_docs && sc >= mn;
+        uint32_t m = __ballot_sync(FULL, hit);
+        if (!m) continue;
+        unsigned long long base = 0;
+        uint32_t leader = __ffs(m) - 1u;
+        if (lane == leader) {
+            base = atomicAdd(a.hit_count, (unsigned long long)__popc(m));
+            atomicAdd(&a.qcount[a.q], (uint32_t)__popc(m));
+        }
+        base = __shfl_sync(FULL, base, leader);
+        if (hit) {
+            unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
+            if (pos < a.hit_cap) {
+                a.raw_q[pos] = a.q;
+                a.raw_key[pos] = ((unsigned long long)(~sc) << 32) | a.perm[p];
+            }
+        }
+    }
+}
+
+void launch_plain_threshold(const ThresholdArgs &a, cudaStream_t s) {
+    uint32_t blocks = (a.n_docs + 255) / 256;
+    if (blocks == 0) return;
+    if (blocks > 1024) blocks = 1024;
+    k_plain_threshold<<<blocks, 256, 0, s>>>(a);
+}
+
+}  // namespace cobs

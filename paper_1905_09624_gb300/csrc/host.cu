@@ -1,0 +1,1061 @@
+// Host runtime and C ABI of the COBS query engine: index planning and device
+// build (Sec. 2.3 "Classic and Compact"), index transfer and files, the query
+// engine with its plain, batched and graph forms, and result assembly.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "host_internal.h"
+
+using namespace cobs;
+
+namespace cobs {
+
+static thread_local std::string g_err;
+
+cobs_status set_error(cobs_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+}  // namespace cobs
+
+#define CU(call)                                                                                        \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return set_error(e_ == cudaErrorMemoryAllocation ? COBS_ERR_OOM : COBS_ERR_CUDA, "%s: %s", \
+                             #call, cudaGetErrorString(e_));                                            \
+    } while (0)
+
+#define TRY(expr)                         \
+    do {                                  \
+        cobs_status s_ = (expr);          \
+        if (s_ != COBS_OK) return s_;     \
+    } while (0)
+
+extern "C" const char *cobs_last_error(void) { return g_err.c_str(); }
+extern "C" const char *cobs_version(void) { return "cobs_gpu 0.1 (sm_103a)"; }
+
+// --------------------------------------------------------------- planning
+
+// Sec. 2.1: the false-positive rate of a filter with w cells, h hashes and v
+// elements is about (1 - e^{-hv/w})^h; solved for w at the target p.
+extern "C" uint64_t cobs_bloom_width(uint32_t h, uint64_t v, double p) {
+    double x = -(double)h * (double)v / std::log(1.0 - std::pow(p, 1.0 / (double)h));
+    double c = std::ceil(x);
+    return c < 1.0 ? 1 : (uint64_t)c;
+}
+
+static cobs_status check_params(const cobs_params *P) {
+    if (!P) return set_error(COBS_ERR_ARG, "params is NULL");
+    if (P->term_kind > 2) return set_error(COBS_ERR_ARG, "term_kind must be 0, 1 or 2");
+    if (P->term_kind == 2 ? (P->q < 1 || P->q > 8) : (P->q < 1 || P->q > 32))
+        return set_error(COBS_ERR_ARG, "q out of range for the term kind");
+    if (P->num_hashes < 1 || P->num_hashes > 16) return set_error(COBS_ERR_ARG, "num_hashes must be 1..16");
+    if (!(P->fpr > 0.0 && P->fpr < 1.0)) return set_error(COBS_ERR_ARG, "fpr must be in (0, 1)");
+    if (P->score_bits != 16 && P->score_bits != 32) return set_error(COBS_ERR_ARG, "score_bits must be 16 or 32");
+    return COBS_OK;
+}
+
+// Classic: one block, input order.  Compact: documents ordered by (distinct
+// terms, id), blocks of B consecutive documents, Bloom size of the largest
+// document of each block (Sec. 2.2, Sec. 2.3).
+static cobs_status plan_index(const cobs_params &P, const std::vector<uint64_t> &v,
+                              std::vector<cobs_block_info> &blocks, std::vector<uint64_t> &perm) {
+    const uint64_t n = v.size();
+    perm.resize(n);
+    std::iota(perm.begin(), perm.end(), 0ULL);
+    if (P.block_docs)
+        std::sort(perm.begin(), perm.end(), [&](uint64_t a, uint64_t b) { return v[a] != v[b] ? v[a] < v[b] : a < b; });
+    const uint64_t B = P.block_docs ? P.block_docs : (n ? n : 1);
+    blocks.clear();
+    uint64_t off = 0;
+    for (uint64_t begin = 0; begin < n; begin += B) {
+        cobs_block_info b{};
+        b.doc_begin = begin;
+        b.n_docs = std::min(B, n - begin);
+        for (uint64_t j = 0; j < b.n_docs; j++) b.max_terms = std::max(b.max_terms, v[perm[begin + j]]);
+        b.w = cobs_bloom_width(P.num_hashes, b.max_terms, P.fpr);
+        if (b.w > 0xFFFFFFFFULL) return set_error(COBS_ERR_ARG, "block %llu needs %llu rows (limit 2^32-1)",
+                                                  (unsigned long long)blocks.size(), (unsigned long long)b.w);
+        b.rowbytes = (b.n_docs + 127) / 128 * 16;
+        b.row_offset = off;
+        off += b.w * b.rowbytes;
+        blocks.push_back(b);
+    }
+    return COBS_OK;
+}
+
+static uint64_t barrett_m_of(uint64_t w) {
+    if (w <= 1) return ~0ULL;
+    unsigned __int128 one = (unsigned __int128)1 << 64;
+    return (uint64_t)(one / w);
+}
+
+// Upload the block table, permutation and column maps of a device index.
+static cobs_status upload_tables(cobs_device_index *dix, cudaStream_t s) {
+    const uint64_t nb = dix->blocks.size();
+    std::vector<DevBlock> db(nb);
+    std::vector<uint32_t> cb, cy;
+    for (uint64_t b = 0; b < nb; b++) {
+        const cobs_block_info &B = dix->blocks[b];
+        db[b].row_offset = B.row_offset;
+        db[b].barrett_m = barrett_m_of(B.w);
+        db[b].w = (uint32_t)B.w;
+        db[b].rowbytes = (uint32_t)B.rowbytes;
+        db[b].n_docs = (uint32_t)B.n_docs;
+        db[b].doc_begin = (uint32_t)B.doc_begin;
+        for (uint64_t c = 0; c < B.rowbytes / 16; c++) {
+            cb.push_back((uint32_t)b);
+            cy.push_back((uint32_t)(c * 16));
+        }
+    }
+    dix->n_cols = (uint32_t)cb.size();
+    std::vector<uint32_t> p32(dix->n_docs);
+    for (uint64_t i = 0; i < dix->n_docs; i++) p32[i] = (uint32_t)dix->perm[i];
+    CU(dix->dblocks.ensure(nb * sizeof(DevBlock)));
+    CU(dix->dperm.ensure(dix->n_docs * 4));
+    CU(dix->col_block.ensure(cb.size() * 4));
+    CU(dix->col_byte.ensure(cy.size() * 4));
+    if (nb) CU(cudaMemcpyAsync(dix->dblocks.p, db.data(), nb * sizeof(DevBlock), cudaMemcpyHostToDevice, s));
+    if (dix->n_docs) CU(cudaMemcpyAsync(dix->dperm.p, p32.data(), dix->n_docs * 4, cudaMemcpyHostToDevice, s));
+    if (!cb.empty()) {
+        CU(cudaMemcpyAsync(dix->col_block.p, cb.data(), cb.size() * 4, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(dix->col_byte.p, cy.data(), cy.size() * 4, cudaMemcpyHostToDevice, s));
+    }
+    CU(cudaStreamSynchronize(s));
+    return COBS_OK;
+}
+
+// ------------------------------------------------------------ device build
+
+static cobs_status build_impl(const cobs_params *P, const uint8_t *d_docs, const uint64_t *d_off,
+                              const uint64_t *h_off, uint64_t n_docs, int device, cudaStream_t s,
+                              cobs_device_index **out) {
+    TRY(check_params(P));
+    if (n_docs >= 0xFFFFFFFFULL) return set_error(COBS_ERR_ARG, "n_docs must be < 2^32");
+    const uint32_t k = P->q;
+    std::vector<uint64_t> npos(n_docs);
+    std::vector<uint32_t> chunk_doc;
+    std::vector<uint64_t> chunk_p0;
+    for (uint64_t d = 0; d < n_docs; d++) {
+        if (h_off[d + 1] < h_off[d]) return set_error(COBS_ERR_ARG, "document offsets decrease at %llu",
+                                                      (unsigned long long)d);
+        uint64_t len = h_off[d + 1] - h_off[d];
+        npos[d] = len >= k ? len - k + 1 : 0;
+        for (uint64_t p = 0; p < npos[d]; p += BUILD_CHUNK) {
+            chunk_doc.push_back((uint32_t)d);
+            chunk_p0.push_back(p);
+        }
+    }
+    const uint64_t n_chunks = chunk_doc.size();
+    if (n_chunks > 0x7FFFFFFFULL) return set_error(COBS_ERR_ARG, "documents too large for one build");
+
+    DevBuf dchunk_doc, dchunk_p0, dv, dempty, dtbase, dtcap, dtables, ddocblk, ddoccol;
+    CU(dchunk_doc.ensure(n_chunks * 4));
+    CU(dchunk_p0.ensure(n_chunks * 8));
+    CU(dv.ensure(n_docs * 8));
+    CU(dempty.ensure(n_docs * 4));
+    CU(dtbase.ensure(n_docs * 8));
+    CU(dtcap.ensure(n_docs * 4));
+    if (n_chunks) {
+        CU(cudaMemcpyAsync(dchunk_doc.p, chunk_doc.data(), n_chunks * 4, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(dchunk_p0.p, chunk_p0.data(), n_chunks * 8, cudaMemcpyHostToDevice, s));
+    }
+    if (n_docs) {
+        CU(cudaMemsetAsync(dv.p, 0, n_docs * 8, s));
+        CU(cudaMemsetAsync(dempty.p, 0, n_docs * 4, s));
+    }
+
+    // Distinct-term counts, in waves of documents whose sets fit a memory budget.
+    size_t free_b = 0, total_b = 0;
+    CU(cudaMemGetInfo(&free_b, &total_b));
+    uint64_t budget = std::min<uint64_t>(free_b / 4, 8ULL << 30) / 8;  // in slots
+    if (budget < (1u << 20)) budget = 1u << 20;
+    std::vector<uint64_t> tbase(n_docs);
+    std::vector<uint32_t> tcap(n_docs);
+    struct Wave { uint64_t d0, d1, c0, c1, slots; };
+    std::vector<Wave> waves;
+    {
+        uint64_t d = 0, c = 0;
+        while (d < n_docs) {
+            Wave wv{d, d, c, c, 0};
+            while (d < n_docs) {
+                uint64_t sl = set_slots(npos[d]);
+                if (sl > 0xFFFFFFFFULL) return set_error(COBS_ERR_ARG, "document %llu too long", (unsigned long long)d);
+                if (wv.d1 > wv.d0 && wv.slots + sl > budget) break;
+                tbase[d] = wv.slots;
+                tcap[d] = (uint32_t)sl;
+                wv.slots += sl;
+                while (c < n_chunks && chunk_doc[c] == d) c++;
+                d++;
+                wv.d1 = d;
+                wv.c1 = c;
+            }
+            waves.push_back(wv);
+        }
+    }
+    uint64_t max_slots = 16;
+    for (const Wave &wv : waves) max_slots = std::max(max_slots, wv.slots);
+    CU(dtables.ensure(max_slots * 8));
+    if (n_docs) {
+        CU(cudaMemcpyAsync(dtbase.p, tbase.data(), n_docs * 8, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(dtcap.p, tcap.data(), n_docs * 4, cudaMemcpyHostToDevice, s));
+    }
+    for (const Wave &wv : waves) {
+        CU(cudaMemsetAsync(dtables.p, 0xFF, wv.slots * 8, s));
+        CountArgs ca{};
+        ca.docs = d_docs;
+        ca.doc_off = d_off;
+        ca.chunk_doc = dchunk_doc.as<uint32_t>() + wv.c0;
+        ca.chunk_p0 = dchunk_p0.as<uint64_t>() + wv.c0;
+        ca.table_base = dtbase.as<uint64_t>();
+        ca.table_cap = dtcap.as<uint32_t>();
+        ca.tables = dtables.as<unsigned long long>();
+        ca.v = dv.as<unsigned long long>();
+        ca.has_empty = dempty.as<uint32_t>();
+        ca.kind = P->term_kind;
+        ca.k = k;
+        launch_doc_count(ca, (uint32_t)(wv.c1 - wv.c0), s);
+        CU(cudaGetLastError());
+    }
+    std::vector<uint64_t> v(n_docs);
+    if (n_docs) CU(cudaMemcpyAsync(v.data(), dv.p, n_docs * 8, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    dtables.release();
+
+    // Plan on the host, then set the Bloom bits on the device.
+    cobs_device_index *dix = new cobs_device_index();
+    dix->params = *P;
+    dix->device = device;
+    dix->n_docs = n_docs;
+    dix->nterms = v;
+    cobs_status st = plan_index(*P, v, dix->blocks, dix->perm);
+    if (st != COBS_OK) { delete dix; return st; }
+    dix->rows_bytes = dix->blocks.empty() ? 0 : dix->blocks.back().row_offset + dix->blocks.back().w * dix->blocks.back().rowbytes;
+    auto fail = [&](cobs_status e) { delete dix; return e; };
+    cudaError_t ce = dix->rows.ensure(dix->rows_bytes);
+    if (ce != cudaSuccess) return fail(set_error(COBS_ERR_OOM, "index rows (%llu bytes): %s",
+                                                 (unsigned long long)dix->rows_bytes, cudaGetErrorString(ce)));
+    if (dix->rows_bytes && (ce = cudaMemsetAsync(dix->rows.p, 0, dix->rows_bytes, s)) != cudaSuccess)
+        return fail(set_error(COBS_ERR_CUDA, "memset rows: %s", cudaGetErrorString(ce)));
+    st = upload_tables(dix, s);
+    if (st != COBS_OK) return fail(st);
+    std::vector<uint32_t> doc_block(n_docs), doc_col(n_docs);
+    for (uint64_t b = 0; b < dix->blocks.size(); b++)
+        for (uint64_t j = 0; j < dix->blocks[b].n_docs; j++) {
+            uint64_t d = dix->perm[dix->blocks[b].doc_begin + j];
+            doc_block[d] = (uint32_t)b;
+            doc_col[d] = (uint32_t)j;
+        }
+    if ((ce = ddocblk.ensure(n_docs * 4)) != cudaSuccess || (ce = ddoccol.ensure(n_docs * 4)) != cudaSuccess)
+        return fail(set_error(COBS_ERR_OOM, "build tables: %s", cudaGetErrorString(ce)));
+    if (n_docs) {
+        cudaMemcpyAsync(ddocblk.p, doc_block.data(), n_docs * 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(ddoccol.p, doc_col.data(), n_docs * 4, cudaMemcpyHostToDevice, s);
+    }
+    SetBitsArgs sa{};
+    sa.docs = d_docs;
+    sa.doc_off = d_off;
+    sa.chunk_doc = dchunk_doc.as<uint32_t>();
+    sa.chunk_p0 = dchunk_p0.as<uint64_t>();
+    sa.doc_block = ddocblk.as<uint32_t>();
+    sa.doc_col = ddoccol.as<uint32_t>();
+    sa.blocks = dix->dblocks.as<DevBlock>();
+    sa.rows32 = dix->rows.as<uint32_t>();
+    sa.kind = P->term_kind;
+    sa.k = k;
+    sa.h = P->num_hashes;
+    launch_doc_setbits(sa, (uint32_t)n_chunks, s);
+    if ((ce = cudaGetLastError()) != cudaSuccess || (ce = cudaStreamSynchronize(s)) != cudaSuccess)
+        return fail(set_error(COBS_ERR_CUDA, "build kernels: %s", cudaGetErrorString(ce)));
+    *out = dix;
+    return COBS_OK;
+}
+
+extern "C" cobs_status cobs_build_device_resident(const cobs_params *params, const uint8_t *docs_dev,
+                                                  const uint64_t *doc_offsets_dev, const uint64_t *doc_offsets_host,
+                                                  uint64_t n_docs, void *stream, cobs_device_index **out) {
+    if (!out || (n_docs && (!docs_dev || !doc_offsets_dev || !doc_offsets_host)))
+        return set_error(COBS_ERR_ARG, "NULL argument");
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    return build_impl(params, docs_dev, doc_offsets_dev, doc_offsets_host, n_docs, dev, (cudaStream_t)stream, out);
+}
+
+extern "C" cobs_status cobs_build_device(const cobs_params *params, const uint8_t *docs, const uint64_t *doc_offsets,
+                                         uint64_t n_docs, int device, void *stream, cobs_device_index **out) {
+    if (!out || !doc_offsets || (n_docs && !docs)) return set_error(COBS_ERR_ARG, "NULL argument");
+    TRY(check_params(params));
+    CU(cudaSetDevice(device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t total = doc_offsets[n_docs];
+    DevBuf dd, doff;
+    CU(dd.ensure(total));
+    CU(doff.ensure((n_docs + 1) * 8));
+    if (total) CU(cudaMemcpyAsync(dd.p, docs, total, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(doff.p, doc_offsets, (n_docs + 1) * 8, cudaMemcpyHostToDevice, s));
+    return build_impl(params, dd.as<uint8_t>(), doff.as<uint64_t>(), doc_offsets, n_docs, device, s, out);
+}
+
+extern "C" cobs_status cobs_device_index_download(const cobs_device_index *dix, cobs_index **out) {
+    if (!dix || !out) return set_error(COBS_ERR_ARG, "NULL argument");
+    CU(cudaSetDevice(dix->device));
+    cobs_index *ix = new cobs_index();
+    ix->params = dix->params;
+    ix->n_docs = dix->n_docs;
+    ix->blocks = dix->blocks;
+    ix->perm = dix->perm;
+    ix->nterms = dix->nterms;
+    ix->rows.resize(dix->rows_bytes);
+    if (dix->rows_bytes) {
+        cudaError_t e = cudaMemcpy(ix->rows.data(), dix->rows.p, dix->rows_bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            delete ix;
+            return set_error(COBS_ERR_CUDA, "download rows: %s", cudaGetErrorString(e));
+        }
+    }
+    *out = ix;
+    return COBS_OK;
+}
+
+extern "C" cobs_status cobs_build(const cobs_params *params, const uint8_t *docs, const uint64_t *doc_offsets,
+                                  uint64_t n_docs, cobs_index **out) {
+    cobs_device_index *dix = nullptr;
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    TRY(cobs_build_device(params, docs, doc_offsets, n_docs, dev, nullptr, &dix));
+    cobs_status s = cobs_device_index_download(dix, out);
+    delete dix;
+    return s;
+}
+
+extern "C" cobs_status cobs_load_device(const cobs_index *ix, int device, void *stream, cobs_device_index **out) {
+    if (!ix || !out) return set_error(COBS_ERR_ARG, "NULL argument");
+    TRY(check_params(&ix->params));
+    CU(cudaSetDevice(device));
+    cobs_device_index *dix = new cobs_device_index();
+    dix->params = ix->params;
+    dix->device = device;
+    dix->n_docs = ix->n_docs;
+    dix->blocks = ix->blocks;
+    dix->perm = ix->perm;
+    dix->nterms = ix->nterms;
+    dix->rows_bytes = ix->rows.size();
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = dix->rows.ensure(dix->rows_bytes);
+    if (e == cudaSuccess && dix->rows_bytes)
+        e = cudaMemcpyAsync(dix->rows.p, ix->rows.data(), dix->rows_bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        delete dix;
+        return set_error(e == cudaErrorMemoryAllocation ? COBS_ERR_OOM : COBS_ERR_CUDA, "load rows: %s",
+                         cudaGetErrorString(e));
+    }
+    cobs_status st = upload_tables(dix, s);
+    if (st != COBS_OK) {
+        delete dix;
+        return st;
+    }
+    *out = dix;
+    return COBS_OK;
+}
+
+extern "C" void cobs_index_free(cobs_index *ix) { delete ix; }
+extern "C" void cobs_device_index_free(cobs_device_index *dix) {
+    if (!dix) return;
+    cudaSetDevice(dix->device);
+    delete dix;
+}
+
+extern "C" cobs_status cobs_index_info(const cobs_index *ix, cobs_params *params, uint64_t *n_docs,
+                                       uint64_t *n_blocks, const cobs_block_info **blocks, const uint64_t **perm,
+                                       const uint64_t **nterms, const uint8_t **rows, uint64_t *rows_bytes) {
+    if (!ix) return set_error(COBS_ERR_ARG, "NULL index");
+    if (params) *params = ix->params;
+    if (n_docs) *n_docs = ix->n_docs;
+    if (n_blocks) *n_blocks = ix->blocks.size();
+    if (blocks) *blocks = ix->blocks.data();
+    if (perm) *perm = ix->perm.data();
+    if (nterms) *nterms = ix->nterms.data();
+    if (rows) *rows = ix->rows.data();
+    if (rows_bytes) *rows_bytes = ix->rows.size();
+    return COBS_OK;
+}
+
+extern "C" cobs_status cobs_device_index_info(const cobs_device_index *dix, cobs_params *params, uint64_t *n_docs,
+                                              uint64_t *n_blocks, const cobs_block_info **blocks,
+                                              const void **rows_dev, uint64_t *rows_bytes) {
+    if (!dix) return set_error(COBS_ERR_ARG, "NULL index");
+    if (params) *params = dix->params;
+    if (n_docs) *n_docs = dix->n_docs;
+    if (n_blocks) *n_blocks = dix->blocks.size();
+    if (blocks) *blocks = dix->blocks.data();
+    if (rows_dev) *rows_dev = dix->rows.p;
+    if (rows_bytes) *rows_bytes = dix->rows_bytes;
+    return COBS_OK;
+}
+
+// ------------------------------------------------------------------ files
+static const char MAGIC[8] = {'C', 'O', 'B', 'S', 'G', 'P', 'U', '1'};
+
+extern "C" cobs_status cobs_index_save(const cobs_index *ix, const char *path) {
+    if (!ix || !path) return set_error(COBS_ERR_ARG, "NULL argument");
+    FILE *f = fopen(path, "wb");
+    if (!f) return set_error(COBS_ERR_ARG, "cannot open %s for writing", path);
+    uint64_t nb = ix->blocks.size(), rb = ix->rows.size();
+    bool ok = fwrite(MAGIC, 8, 1, f) == 1 && fwrite(&ix->params, sizeof(cobs_params), 1, f) == 1 &&
+              fwrite(&ix->n_docs, 8, 1, f) == 1 && fwrite(&nb, 8, 1, f) == 1 && fwrite(&rb, 8, 1, f) == 1;
+    if (ok && nb) ok = fwrite(ix->blocks.data(), sizeof(cobs_block_info), nb, f) == nb;
+    if (ok && ix->n_docs) ok = fwrite(ix->perm.data(), 8, ix->n_docs, f) == ix->n_docs &&
+                               fwrite(ix->nterms.data(), 8, ix->n_docs, f) == ix->n_docs;
+    if (ok && rb) ok = fwrite(ix->rows.data(), 1, rb, f) == rb;
+    if (fclose(f) != 0) ok = false;
+    return ok ? COBS_OK : set_error(COBS_ERR_ARG, "write to %s failed", path);
+}
+
+extern "C" cobs_status cobs_index_load(const char *path, cobs_index **out) {
+    if (!path || !out) return set_error(COBS_ERR_ARG, "NULL argument");
+    FILE *f = fopen(path, "rb");
+    if (!f) return set_error(COBS_ERR_ARG, "cannot open %s", path);
+    cobs_index *ix = new cobs_index();
+    char magic[8];
+    uint64_t nb = 0, rb = 0;
+    bool ok = fread(magic, 8, 1, f) == 1 && memcmp(magic, MAGIC, 8) == 0 &&
+              fread(&ix->params, sizeof(cobs_params), 1, f) == 1 && fread(&ix->n_docs, 8, 1, f) == 1 &&
+              fread(&nb, 8, 1, f) == 1 && fread(&rb, 8, 1, f) == 1;
+    ok = ok && nb <= (1ULL << 32) && ix->n_docs < (1ULL << 32) && rb < (1ULL << 44);
+    if (ok) {
+        ix->blocks.resize(nb);
+        ix->perm.resize(ix->n_docs);
+        ix->nterms.resize(ix->n_docs);
+        ix->rows.resize(rb);
+        ok = (!nb || fread(ix->blocks.data(), sizeof(cobs_block_info), nb, f) == nb) &&
+             (!ix->n_docs || (fread(ix->perm.data(), 8, ix->n_docs, f) == ix->n_docs &&
+                              fread(ix->nterms.data(), 8, ix->n_docs, f) == ix->n_docs)) &&
+             (!rb || fread(ix->rows.data(), 1, rb, f) == rb);
+    }
+    // consistency of the table with the row storage
+    if (ok) {
+        uint64_t off = 0, docs = 0;
+        for (const cobs_block_info &b : ix->blocks) {
+            ok = ok && b.row_offset == off && b.doc_begin == docs && b.rowbytes == (b.n_docs + 127) / 128 * 16 &&
+                 b.w >= 1 && b.w <= 0xFFFFFFFFULL;
+            off += b.w * b.rowbytes;
+            docs += b.n_docs;
+        }
+        ok = ok && off == rb && docs == ix->n_docs;
+        for (uint64_t i = 0; ok && i < ix->n_docs; i++) ok = ix->perm[i] < ix->n_docs;
+    }
+    fclose(f);
+    if (!ok) {
+        delete ix;
+        return set_error(COBS_ERR_FORMAT, "%s is not a complete cobs_gpu index", path);
+    }
+    *out = ix;
+    return COBS_OK;
+}
+
+// ----------------------------------------------------------------- engine
+
+static const uint32_t MAX_CLASSES = 4;
+
+static cobs_status ensure_slices(cobs_engine *eng, uint32_t lpq) {
+    if (eng->slice_lpq == lpq && eng->n_slices) return COBS_OK;
+    std::vector<SliceDesc> sl;
+    const uint32_t S = 16 * lpq;
+    for (uint32_t b = 0; b < eng->dix->blocks.size(); b++)
+        for (uint32_t off = 0; off < eng->dix->blocks[b].rowbytes; off += S) sl.push_back(SliceDesc{b, off});
+    CU(eng->slices.ensure(std::max<size_t>(sl.size(), 1) * sizeof(SliceDesc)));
+    if (!sl.empty())
+        CU(cudaMemcpyAsync(eng->slices.p, sl.data(), sl.size() * sizeof(SliceDesc), cudaMemcpyHostToDevice,
+                           eng->stream));
+    CU(cudaStreamSynchronize(eng->stream));
+    eng->n_slices = (uint32_t)sl.size();
+    eng->slice_lpq = lpq;
+    return COBS_OK;
+}
+
+extern "C" cobs_status cobs_engine_create(cobs_device_index *dix, const cobs_engine_cfg *cfg, void *stream,
+                                          cobs_engine **out) {
+    if (!dix || !out) return set_error(COBS_ERR_ARG, "NULL argument");
+    CU(cudaSetDevice(dix->device));
+    cobs_engine *eng = new cobs_engine();
+    eng->dix = dix;
+    eng->stream = (cudaStream_t)stream;
+    if (!eng->stream) {
+        // graph capture needs a stream other than the legacy default stream
+        cudaError_t e = cudaStreamCreateWithFlags(&eng->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete eng;
+            return set_error(COBS_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+        }
+        eng->own_stream = true;
+    }
+    if (cfg) eng->cfg = *cfg;
+    int dev = dix->device;
+    cudaDeviceGetAttribute(&eng->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    uint32_t sb = eng->cfg.slice_bytes ? eng->cfg.slice_bytes : 128;
+    if (sb != 32 && sb != 64 && sb != 128) {
+        delete eng;
+        return set_error(COBS_ERR_ARG, "slice_bytes must be 32, 64 or 128");
+    }
+    eng->lanes_per_query = sb / 16;
+    int occ = gather_batched_max_blocks_per_sm(eng->lanes_per_query, dix->params.num_hashes);
+    eng->ctas_per_sm = eng->cfg.ctas_per_sm ? eng->cfg.ctas_per_sm : (uint32_t)std::max(occ, 1);
+    eng->hit_cap = eng->cfg.max_hits ? eng->cfg.max_hits : (1ULL << 20);
+    for (auto &e : eng->ev) cudaEventCreate(&e);
+    cudaEventCreateWithFlags(&eng->ev_done, cudaEventDisableTiming);
+    cobs_status st = ensure_slices(eng, eng->lanes_per_query);
+    if (st != COBS_OK) {
+        cobs_engine_free(eng);
+        return st;
+    }
+    *out = eng;
+    return COBS_OK;
+}
+
+extern "C" void cobs_engine_free(cobs_engine *eng) {
+    if (!eng) return;
+    cudaSetDevice(eng->dix->device);
+    if (eng->stream) cudaStreamSynchronize(eng->stream);
+    if (eng->gexec) cudaGraphExecDestroy(eng->gexec);
+    for (auto &e : eng->ev)
+        if (e) cudaEventDestroy(e);
+    if (eng->ev_done) cudaEventDestroy(eng->ev_done);
+    if (eng->own_stream) cudaStreamDestroy(eng->stream);
+    delete eng;
+}
+
+// Plan a batch from the host offsets.
+static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n, BatchPlan &bp) {
+    const cobs_params &P = eng->dix->params;
+    const uint32_t k = P.q;
+    const uint64_t limit = P.score_bits == 16 ? 0xFFFFULL : 0xFFFFFFFFULL;
+    bp.n = n;
+    bp.npos.resize(n);
+    bp.term_base.resize(n);
+    bp.table_base.resize(n);
+    bp.order.resize(n);
+    bp.tcap = 0;
+    bp.total_slots = 0;
+    bp.sum_npos = 0;
+    bp.max_npos = 0;
+    for (uint64_t q = 0; q < n; q++) {
+        if (h_off[q + 1] < h_off[q]) return set_error(COBS_ERR_ARG, "query offsets decrease at %llu", (unsigned long long)q);
+        uint64_t len = h_off[q + 1] - h_off[q];
+        uint64_t np = len >= k ? len - k + 1 : 0;
+        if (np > limit)
+            return set_error(COBS_ERR_OVERFLOW, "query %llu has %llu windows; %u-bit scores count at most %llu",
+                             (unsigned long long)q, (unsigned long long)np, P.score_bits, (unsigned long long)limit);
+        if (np >= (1ULL << 24)) return set_error(COBS_ERR_ARG, "query %llu longer than 2^24 windows", (unsigned long long)q);
+        bp.npos[q] = np;
+        bp.term_base[q] = bp.tcap;
+        bp.tcap += (np + TERM_ALIGN - 1) / TERM_ALIGN * TERM_ALIGN;
+        uint64_t sl = set_slots(np);
+        if (sl > TERMS_SMEM_SLOTS) {
+            bp.table_base[q] = bp.total_slots;
+            bp.total_slots += sl;
+        } else {
+            bp.table_base[q] = 0;
+        }
+        bp.sum_npos += np;
+        bp.max_npos = std::max(bp.max_npos, np);
+    }
+    if (bp.tcap == 0) bp.tcap = TERM_ALIGN;
+    std::iota(bp.order.begin(), bp.order.end(), 0u);
+    std::stable_sort(bp.order.begin(), bp.order.end(),
+                     [&](uint32_t a, uint32_t b) { return bp.npos[a] > bp.npos[b]; });
+    bp.classes.clear();
+    for (uint32_t i = 0; i < n;) {
+        uint32_t L = counter_levels_for((uint32_t)bp.npos[bp.order[i]]);
+        uint32_t j = i;
+        while (j < n && counter_levels_for((uint32_t)bp.npos[bp.order[j]]) == L) j++;
+        bp.classes.push_back({i, j - i, L});
+        i = j;
+    }
+    return COBS_OK;
+}
+
+static cobs_status ensure_buffers(cobs_engine *eng, const BatchPlan &bp) {
+    const uint64_t n = bp.n;
+    const uint64_t nb = eng->dix->blocks.size(), h = eng->dix->params.num_hashes;
+    CU(eng->plan.ensure(n * 20 + 64));
+    CU(eng->ell.ensure(n * 4));
+    CU(eng->minsc.ensure(n * 4));
+    CU(eng->qcount.ensure(n * 4 + 64 * 8));  // qcount, then the counters (one memset clears both)
+    CU(eng->qcursor.ensure(n * 4));
+    CU(eng->hitoff.ensure((n + 1) * 8));
+    CU(eng->rows_idx.ensure(std::max<uint64_t>(nb, 1) * h * bp.tcap * 4));
+    CU(eng->tables.ensure(bp.total_slots * 8));
+    CU(eng->raw_q.ensure(eng->hit_cap * 4));
+    CU(eng->raw_key.ensure(eng->hit_cap * 8));
+    CU(eng->keys.ensure(eng->hit_cap * 8));
+    CU(eng->tmp.ensure(eng->hit_cap * 8));
+    CU(eng->out_ids.ensure(eng->hit_cap * 4));
+    CU(eng->out_scores.ensure(eng->hit_cap * 4));
+    CU(eng->scores.ensure(eng->dix->n_docs * 4));
+    CU(eng->pin_plan.ensure(n * 20 + 64));
+    CU(eng->pin_count.ensure(64));
+    return COBS_OK;
+}
+
+static unsigned long long *counters_of(cobs_engine *eng, uint64_t n) {
+    // counters live right after the n query counts, 8-byte aligned
+    uintptr_t p = (uintptr_t)(eng->qcount.as<uint8_t>() + n * 4);
+    p = (p + 7) & ~(uintptr_t)7;
+    return (unsigned long long *)p;
+}
+
+// Enqueue the whole query sequence on the engine stream.
+static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint64_t *d_off, const uint16_t *d_thr,
+                           uint32_t flags, bool timed) {
+    cobs_device_index *dix = eng->dix;
+    const BatchPlan &bp = eng->bp;
+    const uint64_t n = bp.n;
+    const cobs_params &P = dix->params;
+    cudaStream_t s = eng->stream;
+    uint8_t *plan = eng->plan.as<uint8_t>();
+    const uint64_t *term_base = (const uint64_t *)plan;
+    const uint64_t *table_base = (const uint64_t *)(plan + n * 8);
+    const uint32_t *order = (const uint32_t *)(plan + n * 16);
+    unsigned long long *ctr = counters_of(eng, n);
+    eng->stat_launches = 0;
+    eng->stat_gather_launches = 0;
+    eng->stat_tiles = 0;
+
+    if (timed) CU(cudaEventRecord(eng->ev[0], s));
+    CU(cudaMemsetAsync(eng->qcount.p, 0, (uint8_t *)(ctr + 16) - eng->qcount.as<uint8_t>(), s));
+    CU(cudaMemcpyAsync(plan, eng->pin_plan.p, n * 20, cudaMemcpyHostToDevice, s));
+
+    TermsArgs ta{};
+    ta.bytes = d_bytes;
+    ta.offsets = d_off;
+    ta.term_base = term_base;
+    ta.table_base = table_base;
+    ta.tables = eng->tables.as<unsigned long long>();
+    ta.ell = eng->ell.as<uint32_t>();
+    ta.rows_idx = eng->rows_idx.as<uint32_t>();
+    ta.tcap = bp.tcap;
+    ta.blocks = dix->dblocks.as<DevBlock>();
+    ta.n_blocks = (uint32_t)dix->blocks.size();
+    ta.h = P.num_hashes;
+    ta.kind = P.term_kind;
+    ta.k = P.q;
+
+    if (flags & COBS_PLAIN) {
+        // One query per kernel sequence: terms, zero scores, gather, threshold.
+        if (timed) CU(cudaEventRecord(eng->ev[1], s));
+        for (uint64_t q = 0; q < n; q++) {
+            ta.q0 = (uint32_t)q;
+            launch_query_terms(ta, 1, s);
+            CU(cudaMemsetAsync(eng->scores.p, 0, dix->n_docs * 4, s));
+            PlainArgs pa{};
+            pa.rows = dix->rows.as<uint8_t>();
+            pa.blocks = dix->dblocks.as<DevBlock>();
+            pa.col_block = dix->col_block.as<uint32_t>();
+            pa.col_byte = dix->col_byte.as<uint32_t>();
+            pa.n_cols = dix->n_cols;
+            pa.rows_idx = eng->rows_idx.as<uint32_t>();
+            pa.tcap = bp.tcap;
+            pa.term_base = term_base;
+            pa.ell = eng->ell.as<uint32_t>();
+            pa.h = P.num_hashes;
+            pa.q = (uint32_t)q;
+            pa.scores = eng->scores.as<uint32_t>();
+            uint32_t chunks = (uint32_t)((bp.npos[q] + PLAIN_CHUNK - 1) / PLAIN_CHUNK);
+            launch_gather_plain(pa, chunks, s);
+            ThresholdArgs th{};
+            th.scores = eng->scores.as<uint32_t>();
+            th.perm = dix->dperm.as<uint32_t>();
+            th.n_docs = (uint32_t)dix->n_docs;
+            th.ell = eng->ell.as<uint32_t>();
+            th.thr = d_thr;
+            th.q = (uint32_t)q;
+            th.hit_count = ctr;
+            th.qcount = eng->qcount.as<uint32_t>();
+            th.raw_q = eng->raw_q.as<uint32_t>();
+            th.raw_key = eng->raw_key.as<unsigned long long>();
+            th.hit_cap = eng->hit_cap;
+            launch_plain_threshold(th, s);
+            eng->stat_launches += 3 + (chunks ? 1 : 0);
+            eng->stat_gather_launches += chunks ? 1 : 0;
+        }
+        CU(cudaGetLastError());
+        if (timed) CU(cudaEventRecord(eng->ev[2], s));
+    } else {
+        ta.q0 = 0;
+        launch_query_terms(ta, (uint32_t)n, s);
+        eng->stat_launches += 1;
+        CU(cudaGetLastError());
+        if (timed) CU(cudaEventRecord(eng->ev[1], s));
+        const uint32_t qpw = 32 / eng->lanes_per_query;
+        const uint32_t grid = (uint32_t)eng->n_sm * eng->ctas_per_sm;
+        for (size_t c = 0; c < bp.classes.size(); c++) {
+            const BatchPlan::Class &cl = bp.classes[c];
+            GatherArgs ga{};
+            ga.rows = dix->rows.as<uint8_t>();
+            ga.blocks = dix->dblocks.as<DevBlock>();
+            ga.perm = dix->dperm.as<uint32_t>();
+            ga.rows_idx = eng->rows_idx.as<uint32_t>();
+            ga.tcap = bp.tcap;
+            ga.term_base = term_base;
+            ga.ell = eng->ell.as<uint32_t>();
+            ga.thr = d_thr;
+            ga.order = order + cl.begin;
+            ga.n_queries = cl.count;
+            ga.h = P.num_hashes;
+            ga.slices = eng->slices.as<SliceDesc>();
+            ga.n_slices = eng->n_slices;
+            ga.n_groups = (cl.count + qpw - 1) / qpw;
+            ga.work_counter = ctr + 1 + (c % 15);
+            ga.hit_count = ctr;
+            ga.qcount = eng->qcount.as<uint32_t>();
+            ga.raw_q = eng->raw_q.as<uint32_t>();
+            ga.raw_key = eng->raw_key.as<unsigned long long>();
+            ga.hit_cap = eng->hit_cap;
+            if (ga.n_slices == 0 || ga.n_groups == 0) continue;
+            launch_gather_batched_L(ga, eng->lanes_per_query, cl.L, grid, s);
+            eng->stat_launches += 1;
+            eng->stat_gather_launches += 1;
+            eng->stat_tiles += (uint64_t)ga.n_slices * ga.n_groups;
+        }
+        CU(cudaGetLastError());
+        if (timed) CU(cudaEventRecord(eng->ev[2], s));
+    }
+    HitsArgs ha{};
+    ha.n_queries = (uint32_t)n;
+    ha.ell = eng->ell.as<uint32_t>();
+    ha.thr = d_thr;
+    ha.min_score = eng->minsc.as<uint32_t>();
+    ha.qcount = eng->qcount.as<uint32_t>();
+    ha.qcursor = eng->qcursor.as<uint32_t>();
+    ha.hit_off = eng->hitoff.as<uint64_t>();
+    ha.hit_count = ctr;
+    ha.hit_cap = eng->hit_cap;
+    ha.raw_q = eng->raw_q.as<uint32_t>();
+    ha.raw_key = eng->raw_key.as<unsigned long long>();
+    ha.keys = eng->keys.as<unsigned long long>();
+    ha.tmp = eng->tmp.as<unsigned long long>();
+    ha.out_ids = eng->out_ids.as<uint32_t>();
+    ha.out_scores = eng->out_scores.as<uint32_t>();
+    launch_hits_finalize(ha, s);
+    eng->stat_launches += 3;
+    CU(cudaGetLastError());
+    if (timed) CU(cudaEventRecord(eng->ev[3], s));
+    CU(cudaMemcpyAsync(eng->pin_count.p, ctr, 8, cudaMemcpyDeviceToHost, s));
+    return COBS_OK;
+}
+
+static void fill_pinned_plan(cobs_engine *eng) {
+    const BatchPlan &bp = eng->bp;
+    uint8_t *p = eng->pin_plan.as<uint8_t>();
+    memcpy(p, bp.term_base.data(), bp.n * 8);
+    memcpy(p + bp.n * 8, bp.table_base.data(), bp.n * 8);
+    memcpy(p + bp.n * 16, bp.order.data(), bp.n * 4);
+}
+
+static std::vector<uint64_t> graph_signature(cobs_engine *eng, const uint8_t *d_bytes, const uint64_t *d_off,
+                                             const uint16_t *d_thr) {
+    const BatchPlan &bp = eng->bp;
+    std::vector<uint64_t> sig = {bp.n, bp.tcap, bp.total_slots, (uint64_t)d_bytes, (uint64_t)d_off, (uint64_t)d_thr,
+                                 eng->hit_cap, eng->lanes_per_query, eng->ctas_per_sm,
+                                 (uint64_t)eng->rows_idx.p, (uint64_t)eng->tables.p, (uint64_t)eng->raw_q.p,
+                                 (uint64_t)eng->plan.p, (uint64_t)eng->pin_plan.p, (uint64_t)eng->qcount.p,
+                                 (uint64_t)eng->ell.p, (uint64_t)eng->minsc.p, (uint64_t)eng->qcursor.p,
+                                 (uint64_t)eng->hitoff.p, (uint64_t)eng->raw_key.p, (uint64_t)eng->keys.p,
+                                 (uint64_t)eng->tmp.p, (uint64_t)eng->out_ids.p, (uint64_t)eng->out_scores.p,
+                                 (uint64_t)eng->pin_count.p, (uint64_t)eng->slices.p, eng->n_slices};
+    for (const auto &c : bp.classes) {
+        sig.push_back(c.begin);
+        sig.push_back(c.count);
+        sig.push_back(c.L);
+    }
+    return sig;
+}
+
+namespace cobs {
+
+cobs_status engine_query(cobs_engine *eng, const uint8_t *d_bytes, const uint64_t *d_off, const uint64_t *h_off,
+                         const uint16_t *d_thr, uint64_t n, uint32_t flags) {
+    if (!eng || (n && (!d_bytes || !d_off || !h_off || !d_thr))) return set_error(COBS_ERR_ARG, "NULL argument");
+    if (flags != COBS_PLAIN && flags != COBS_BATCHED && flags != COBS_GRAPH && flags != (COBS_GRAPH | COBS_BATCHED))
+        return set_error(COBS_ERR_ARG, "flags must be COBS_PLAIN, COBS_BATCHED or COBS_GRAPH");
+    if (n >= 0x7FFFFFFFULL) return set_error(COBS_ERR_ARG, "too many queries in one batch");
+    CU(cudaSetDevice(eng->dix->device));
+    TRY(make_plan(eng, h_off, n, eng->bp));
+    TRY(ensure_buffers(eng, eng->bp));
+    eng->last_bytes = d_bytes;
+    eng->last_off = d_off;
+    eng->last_thr = d_thr;
+    eng->last_off_host.assign(h_off, h_off + n + 1);
+    eng->last_flags = flags;
+    if (n == 0) {
+        eng->pending = false;
+        return COBS_OK;
+    }
+    fill_pinned_plan(eng);
+    if (flags & COBS_GRAPH) {
+        std::vector<uint64_t> sig = graph_signature(eng, d_bytes, d_off, d_thr);
+        if (!eng->gexec || sig != eng->gsig) {
+            if (eng->gexec) {
+                cudaGraphExecDestroy(eng->gexec);
+                eng->gexec = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            CU(cudaStreamBeginCapture(eng->stream, cudaStreamCaptureModeThreadLocal));
+            cobs_status st = enqueue(eng, d_bytes, d_off, d_thr, COBS_BATCHED, false);
+            cudaError_t ce = cudaStreamEndCapture(eng->stream, &g);
+            if (st != COBS_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            if (ce != cudaSuccess) return set_error(COBS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&eng->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) {
+                eng->gexec = nullptr;
+                return set_error(COBS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+            }
+            eng->gsig = sig;
+        }
+        CU(cudaEventRecord(eng->ev[0], eng->stream));
+        CU(cudaGraphLaunch(eng->gexec, eng->stream));
+        CU(cudaEventRecord(eng->ev[3], eng->stream));
+        eng->stat_launches = 1;
+    } else {
+        TRY(enqueue(eng, d_bytes, d_off, d_thr, flags, true));
+    }
+    CU(cudaEventRecord(eng->ev_done, eng->stream));
+    eng->pending = true;
+    return COBS_OK;
+}
+
+// Wait for the last batch; if its hits overflowed the capacity, grow and re-run.
+cobs_status engine_finish(cobs_engine *eng) {
+    if (!eng->pending) return COBS_OK;
+    for (int attempt = 0; attempt < 4; attempt++) {
+        CU(cudaEventSynchronize(eng->ev_done));
+        unsigned long long cnt = *eng->pin_count.as<unsigned long long>();
+        if (cnt <= eng->hit_cap) {
+            eng->pending = false;
+            return COBS_OK;
+        }
+        uint64_t cap = eng->hit_cap;
+        while (cap < cnt) cap *= 2;
+        eng->hit_cap = cap;
+        TRY(ensure_buffers(eng, eng->bp));
+        uint32_t fl = eng->last_flags;
+        TRY(engine_query(eng, eng->last_bytes, eng->last_off, eng->last_off_host.data(), eng->last_thr, eng->bp.n, fl));
+    }
+    return set_error(COBS_ERR_CUDA, "hit capacity kept overflowing");
+}
+
+}  // namespace cobs
+
+extern "C" cobs_status cobs_engine_query_device(cobs_engine *eng, const uint8_t *queries_dev,
+                                                const uint64_t *offsets_dev, const uint64_t *offsets_host,
+                                                const uint16_t *thr_dev, uint64_t n, uint32_t flags) {
+    return engine_query(eng, queries_dev, offsets_dev, offsets_host, thr_dev, n, flags);
+}
+
+extern "C" cobs_status cobs_engine_results_device(cobs_engine *eng, const uint32_t **n_terms,
+                                                  const uint32_t **min_score, const uint64_t **hit_offsets,
+                                                  const uint32_t **hit_ids, const uint32_t **hit_scores) {
+    if (!eng) return set_error(COBS_ERR_ARG, "NULL engine");
+    TRY(engine_finish(eng));
+    if (n_terms) *n_terms = eng->ell.as<uint32_t>();
+    if (min_score) *min_score = eng->minsc.as<uint32_t>();
+    if (hit_offsets) *hit_offsets = eng->hitoff.as<uint64_t>();
+    if (hit_ids) *hit_ids = eng->out_ids.as<uint32_t>();
+    if (hit_scores) *hit_scores = eng->out_scores.as<uint32_t>();
+    return COBS_OK;
+}
+
+namespace cobs {
+struct ResultStore {
+    cobs_result pub;
+    std::vector<cobs_hits> hits;
+    std::vector<uint32_t> ids, scores;
+};
+}  // namespace cobs
+
+extern "C" cobs_status cobs_engine_download(cobs_engine *eng, cobs_result **out) {
+    if (!eng || !out) return set_error(COBS_ERR_ARG, "NULL argument");
+    TRY(engine_finish(eng));
+    const uint64_t n = eng->bp.n;
+    ResultStore *rs = new ResultStore();
+    std::vector<uint32_t> ell(n), mn(n);
+    std::vector<uint64_t> off(n + 1, 0);
+    cudaStream_t s = eng->stream;
+    cudaError_t e = cudaSuccess;
+    if (n) {
+        e = cudaMemcpyAsync(ell.data(), eng->ell.p, n * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(mn.data(), eng->minsc.p, n * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(off.data(), eng->hitoff.p, (n + 1) * 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    const uint64_t total = off[n];
+    if (e == cudaSuccess && total) {
+        rs->ids.resize(total);
+        rs->scores.resize(total);
+        e = cudaMemcpyAsync(rs->ids.data(), eng->out_ids.p, total * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rs->scores.data(), eng->out_scores.p, total * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) {
+        delete rs;
+        return set_error(COBS_ERR_CUDA, "download results: %s", cudaGetErrorString(e));
+    }
+    rs->hits.resize(n);
+    for (uint64_t q = 0; q < n; q++) {
+        cobs_hits &h = rs->hits[q];
+        h.n_terms = ell[q];
+        h.min_score = mn[q];
+        h.n_hits = (uint32_t)(off[q + 1] - off[q]);
+        h._pad = 0;
+        h.doc_ids = total ? rs->ids.data() + off[q] : nullptr;
+        h.scores = total ? rs->scores.data() + off[q] : nullptr;
+    }
+    rs->pub.n_queries = n;
+    rs->pub.hits = rs->hits.data();
+    *out = &rs->pub;
+    return COBS_OK;
+}
+
+extern "C" void cobs_result_free(cobs_result *res) {
+    if (!res) return;
+    delete reinterpret_cast<ResultStore *>(reinterpret_cast<char *>(res) - offsetof(ResultStore, pub));
+}
+
+static cobs_status check_thresholds(const uint16_t *thr, uint64_t n) {
+    for (uint64_t i = 0; i < n; i++)
+        if (thr[i] == 0 || thr[i] > 1000)
+            return set_error(COBS_ERR_ARG, "threshold of query %llu is %u permille (must be 1..1000)",
+                             (unsigned long long)i, thr[i]);
+    return COBS_OK;
+}
+
+extern "C" cobs_status cobs_engine_query_host(cobs_engine *eng, const uint8_t *queries, const uint64_t *offsets,
+                                              const uint16_t *thr, uint64_t n, uint32_t flags, cobs_result **out) {
+    if (!eng || !offsets || !out || (n && (!thr || !queries))) return set_error(COBS_ERR_ARG, "NULL argument");
+    TRY(check_thresholds(thr, n));
+    CU(cudaSetDevice(eng->dix->device));
+    const uint64_t total = offsets[n];
+    const uint64_t in_bytes = total + (n + 1) * 8 + n * 2 + 64;
+    CU(eng->pin_in.ensure(in_bytes));
+    CU(eng->qbytes.ensure(total));
+    CU(eng->qoff.ensure((n + 1) * 8));
+    CU(eng->thr.ensure(n * 2 + 16));
+    uint8_t *pin = eng->pin_in.as<uint8_t>();
+    if (total) memcpy(pin, queries, total);
+    uint64_t o1 = (total + 15) / 16 * 16, o2 = o1 + (n + 1) * 8;
+    memcpy(pin + o1, offsets, (n + 1) * 8);
+    if (n) memcpy(pin + o2, thr, n * 2);
+    cudaStream_t s = eng->stream;
+    if (total) CU(cudaMemcpyAsync(eng->qbytes.p, pin, total, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(eng->qoff.p, pin + o1, (n + 1) * 8, cudaMemcpyHostToDevice, s));
+    if (n) CU(cudaMemcpyAsync(eng->thr.p, pin + o2, n * 2, cudaMemcpyHostToDevice, s));
+    TRY(engine_query(eng, eng->qbytes.as<uint8_t>(), eng->qoff.as<uint64_t>(), offsets, eng->thr.as<uint16_t>(), n,
+                     flags));
+    return cobs_engine_download(eng, out);
+}
+
+extern "C" cobs_status cobs_query_batch(cobs_device_index *dix, const uint8_t *queries, const uint64_t *query_offsets,
+                                        const uint16_t *threshold_permille, uint64_t n, uint32_t flags, void *stream,
+                                        cobs_result **out) {
+    if (!dix || !query_offsets || !out) return set_error(COBS_ERR_ARG, "NULL argument");
+    cobs_engine_cfg cfg{};
+    cfg.max_queries = n;
+    cfg.max_query_bytes = query_offsets[n];
+    cobs_engine *eng = nullptr;
+    TRY(cobs_engine_create(dix, &cfg, stream, &eng));
+    cobs_status st = cobs_engine_query_host(eng, queries, query_offsets, threshold_permille, n, flags, out);
+    cobs_engine_free(eng);
+    return st;
+}
+
+extern "C" cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out) {
+    if (!eng || !out) return set_error(COBS_ERR_ARG, "NULL argument");
+    TRY(engine_finish(eng));
+    memset(out, 0, sizeof *out);
+    float t = 0;
+    if (eng->last_flags & COBS_GRAPH) {
+        cudaEventElapsedTime(&t, eng->ev[0], eng->ev[3]);
+        out->ms_total = t;
+    } else if (eng->bp.n) {
+        cudaEventElapsedTime(&t, eng->ev[0], eng->ev[1]); out->ms_terms = t;
+        cudaEventElapsedTime(&t, eng->ev[1], eng->ev[2]); out->ms_gather = t;
+        cudaEventElapsedTime(&t, eng->ev[2], eng->ev[3]); out->ms_hits = t;
+        cudaEventElapsedTime(&t, eng->ev[0], eng->ev[3]); out->ms_total = t;
+    }
+    const cobs_device_index *dix = eng->dix;
+    uint64_t rb = 0;
+    for (const auto &b : dix->blocks) rb += b.rowbytes;
+    std::vector<uint32_t> ell(eng->bp.n);
+    if (eng->bp.n) CU(cudaMemcpy(ell.data(), eng->ell.p, eng->bp.n * 4, cudaMemcpyDeviceToHost));
+    uint64_t terms = 0;
+    for (uint32_t e : ell) terms += e;
+    out->terms = terms;
+    out->row_bytes = terms * rb * dix->params.num_hashes;
+    out->n_tiles = eng->stat_tiles;
+    out->gather_launches = eng->stat_gather_launches;
+    out->launches = eng->stat_launches;
+    out->slice_bytes = eng->lanes_per_query * 16;
+    out->ctas_per_sm = eng->ctas_per_sm;
+    return COBS_OK;
+}
+
+extern "C" cobs_status cobs_engine_autotune(cobs_engine *eng, const uint8_t *queries_dev, const uint64_t *offsets_dev,
+                                            const uint64_t *offsets_host, const uint16_t *thr_dev, uint64_t n,
+                                            cobs_engine_cfg *cfg_out) {
+    if (!eng) return set_error(COBS_ERR_ARG, "NULL engine");
+    const uint32_t lpqs[3] = {2, 4, 8};
+    double best = 1e30;
+    uint32_t best_lpq = eng->lanes_per_query, best_cta = eng->ctas_per_sm;
+    const int occ_max = std::max(1, gather_batched_max_blocks_per_sm(8, eng->dix->params.num_hashes));
+    for (uint32_t lpq : lpqs) {
+        TRY(ensure_slices(eng, lpq));
+        eng->lanes_per_query = lpq;
+        for (int cta = 1; cta <= occ_max; cta *= 2) {
+            eng->ctas_per_sm = (uint32_t)cta;
+            double tot = 0;
+            for (int rep = 0; rep < 3; rep++) {
+                TRY(engine_query(eng, queries_dev, offsets_dev, offsets_host, thr_dev, n, COBS_BATCHED));
+                TRY(engine_finish(eng));
+                float t = 0;
+                cudaEventElapsedTime(&t, eng->ev[1], eng->ev[2]);
+                if (rep) tot += t;
+            }
+            if (tot < best) {
+                best = tot;
+                best_lpq = lpq;
+                best_cta = (uint32_t)cta;
+            }
+            if (cta < occ_max && cta * 2 > occ_max) cta = occ_max / 2;  // also try the full occupancy
+        }
+    }
+    TRY(ensure_slices(eng, best_lpq));
+    eng->lanes_per_query = best_lpq;
+    eng->ctas_per_sm = best_cta;
+    if (eng->gexec) {
+        cudaGraphExecDestroy(eng->gexec);
+        eng->gexec = nullptr;
+    }
+    if (cfg_out) {
+        *cfg_out = eng->cfg;
+        cfg_out->slice_bytes = best_lpq * 16;
+        cfg_out->ctas_per_sm = best_cta;
+    }
+    return COBS_OK;
+}

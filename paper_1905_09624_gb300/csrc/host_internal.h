@@ -1,0 +1,151 @@
+// Host-side objects of the library (index, device index, engine), shared by the
+// runtime and the serve loop.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "cobs_gpu.h"
+#include "kernels.cuh"
+
+namespace cobs {
+
+cobs_status set_error(cobs_status s, const char *fmt, ...);
+
+// Device allocation that only grows.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t n) {
+        if (n == 0) n = 16;
+        if (n <= bytes) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        else p = nullptr;
+        return e;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Pinned host allocation that only grows.
+struct PinBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    PinBuf() = default;
+    PinBuf(const PinBuf &) = delete;
+    PinBuf &operator=(const PinBuf &) = delete;
+    ~PinBuf() { release(); }
+    void release() {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t n) {
+        if (n == 0) n = 16;
+        if (n <= bytes) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMallocHost(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        else p = nullptr;
+        return e;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Query batch plan (host): term regions, set regions, processing order and the
+// counter-width classes of the batched kernel.
+struct BatchPlan {
+    uint64_t n = 0;
+    std::vector<uint64_t> npos;
+    std::vector<uint64_t> term_base, table_base;
+    std::vector<uint32_t> order;
+    struct Class {
+        uint32_t begin, count, L;
+    };
+    std::vector<Class> classes;
+    uint64_t tcap = 0, total_slots = 0, sum_npos = 0, max_npos = 0;
+};
+
+struct ResultStore;
+
+}  // namespace cobs
+
+struct cobs_index {
+    cobs_params params{};
+    uint64_t n_docs = 0;
+    std::vector<cobs_block_info> blocks;
+    std::vector<uint64_t> perm, nterms;
+    std::vector<uint8_t> rows;
+};
+
+struct cobs_device_index {
+    cobs_params params{};
+    int device = 0;
+    uint64_t n_docs = 0;
+    std::vector<cobs_block_info> blocks;
+    std::vector<uint64_t> perm, nterms;
+    uint64_t rows_bytes = 0;
+    uint32_t n_cols = 0;  // 16-byte columns over all blocks (plain kernel)
+    cobs::DevBuf rows, dblocks, dperm, col_block, col_byte;
+};
+
+struct cobs_engine {
+    cobs_device_index *dix = nullptr;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cobs_engine_cfg cfg{};
+    int n_sm = 0;
+    uint32_t lanes_per_query = 8;
+    uint32_t ctas_per_sm = 1;
+    uint64_t hit_cap = 0;
+
+    // per batch
+    cobs::DevBuf qbytes, qoff, thr;          // staging of host queries
+    cobs::DevBuf plan;                        // term_base | table_base | order
+    cobs::DevBuf ell, minsc, qcount, qcursor, hitoff;
+    cobs::DevBuf counters;                    // [0] hit count, [1..] work counters
+    cobs::DevBuf rows_idx, tables;
+    cobs::DevBuf raw_q, raw_key, keys, tmp, out_ids, out_scores;
+    cobs::DevBuf scores;                      // plain form, per sorted position
+    cobs::DevBuf slices;
+    uint32_t n_slices = 0, slice_lpq = 0;
+    cobs::PinBuf pin_plan, pin_count, pin_in;
+
+    cobs::BatchPlan bp;
+    // last batch (for re-runs after a hit-capacity overflow)
+    const uint8_t *last_bytes = nullptr;
+    const uint64_t *last_off = nullptr;
+    const uint16_t *last_thr = nullptr;
+    std::vector<uint64_t> last_off_host;
+    uint32_t last_flags = 0;
+    bool pending = false;
+
+    // CUDA graph of the batched sequence
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<uint64_t> gsig;
+
+    // timing
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_done = nullptr;
+    uint64_t stat_launches = 0, stat_gather_launches = 0, stat_tiles = 0;
+    uint64_t hit_off_cache = 0;
+};
+
+namespace cobs {
+// Engine operations used by the serve loop.
+cobs_status engine_query(cobs_engine *eng, const uint8_t *d_bytes, const uint64_t *d_off, const uint64_t *h_off,
+                         const uint16_t *d_thr, uint64_t n, uint32_t flags);
+cobs_status engine_finish(cobs_engine *eng);
+}  // namespace cobs

@@ -1,0 +1,151 @@
+// Launch wrappers of the COBS kernels (host-callable, defined in the .cu files).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace cobs {
+
+// Query-term table: shared-memory slots per CTA before the set spills to global memory.
+constexpr uint32_t TERMS_SMEM_SLOTS = 4096;   // 32 KB
+constexpr uint32_t TERMS_THREADS = 256;
+constexpr uint32_t TERMS_SEG = 64;            // positions per rolling segment
+
+struct TermsArgs {
+    const uint8_t *bytes;          // queries concatenated
+    const uint64_t *offsets;       // n + 1 (device)
+    const uint64_t *term_base;     // per query: first slot in the term arrays (multiple of TERM_ALIGN)
+    const uint64_t *table_base;    // per query: first slot of its global set (if it spills)
+    unsigned long long *tables;    // global sets
+    uint32_t *ell;                 // out: distinct terms per query
+    uint32_t *rows_idx;            // out: row of term t for (block b, hash i) at [(b*h+i)*tcap + base + t]
+    uint64_t tcap;
+    const DevBlock *blocks;
+    uint32_t n_blocks, h, kind, k;
+    uint32_t q0;                   // first query handled by blockIdx.x == 0
+};
+void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s);
+
+// Batched gather/AND/ADD with fused threshold (persistent).
+struct SliceDesc {
+    uint32_t block;      // block index
+    uint32_t byte_off;   // byte offset of the slice within a row
+};
+struct GatherArgs {
+    const uint8_t *rows;
+    const DevBlock *blocks;
+    const uint32_t *perm;          // sorted position -> original id
+    const uint32_t *rows_idx;
+    uint64_t tcap;
+    const uint64_t *term_base;
+    const uint32_t *ell;
+    const uint16_t *thr;
+    const uint32_t *order;         // queries in processing order (longest first)
+    uint32_t n_queries;
+    uint32_t h;
+    const SliceDesc *slices;
+    uint32_t n_slices;
+    uint32_t n_groups;             // ceil(n_queries / queries-per-warp)
+    unsigned long long *work_counter;
+    unsigned long long *hit_count;
+    uint32_t *qcount;              // hits per query
+    uint32_t *raw_q;               // raw hits: query
+    unsigned long long *raw_key;   // raw hits: (~score << 32) | original id
+    uint64_t hit_cap;
+};
+// lanes_per_query in {2, 4, 8}: slice = 16 * lanes_per_query bytes.  L = counter
+// levels (8, 12, 16 or 24): every query of the launch has fewer than 2^L terms.
+void launch_gather_batched_L(const GatherArgs &a, uint32_t lanes_per_query, uint32_t L, uint32_t grid,
+                             cudaStream_t s);
+uint32_t counter_levels_for(uint32_t max_terms);
+int gather_batched_max_blocks_per_sm(uint32_t lanes_per_query, uint32_t h);
+// Term arrays: every query's region starts at a multiple of TERM_ALIGN slots and
+// spans a multiple of TERM_ALIGN slots (the gather reads row indices 16 at a time).
+constexpr uint64_t TERM_ALIGN = 16;
+
+// Plain form: one query, term chunks x 16-byte columns, partial scores by atomics.
+constexpr uint32_t PLAIN_CHUNK = 128;   // terms per chunk
+constexpr uint32_t PLAIN_THREADS = 128;
+struct PlainArgs {
+    const uint8_t *rows;
+    const DevBlock *blocks;
+    const uint32_t *col_block;     // per 16-byte column (over all blocks): block index
+    const uint32_t *col_byte;      // per 16-byte column: byte offset within the row
+    uint32_t n_cols;
+    const uint32_t *rows_idx;
+    uint64_t tcap;
+    const uint64_t *term_base;     // of the query
+    const uint32_t *ell;           // of the query
+    uint32_t h;
+    uint32_t q;                    // query index (for term_base / ell)
+    uint32_t *scores;              // per sorted position, zeroed before
+};
+void launch_gather_plain(const PlainArgs &a, uint32_t n_chunks, cudaStream_t s);
+
+struct ThresholdArgs {
+    const uint32_t *scores;
+    const uint32_t *perm;
+    uint32_t n_docs;
+    const uint32_t *ell;
+    const uint16_t *thr;
+    uint32_t q;
+    unsigned long long *hit_count;
+    uint32_t *qcount;
+    uint32_t *raw_q;
+    unsigned long long *raw_key;
+    uint64_t hit_cap;
+};
+void launch_plain_threshold(const ThresholdArgs &a, cudaStream_t s);
+
+// Hit finalisation: per-query offsets, scatter, sort (score desc, id asc), unpack.
+struct HitsArgs {
+    uint32_t n_queries;
+    const uint32_t *ell;
+    const uint16_t *thr;
+    uint32_t *min_score;
+    const uint32_t *qcount;
+    uint32_t *qcursor;
+    uint64_t *hit_off;             // n + 1
+    const unsigned long long *hit_count;
+    uint64_t hit_cap;
+    const uint32_t *raw_q;
+    const unsigned long long *raw_key;
+    unsigned long long *keys;      // scattered keys
+    unsigned long long *tmp;       // sort scratch (same size)
+    uint32_t *out_ids;
+    uint32_t *out_scores;
+};
+void launch_hits_finalize(const HitsArgs &a, cudaStream_t s);
+
+// Device build: distinct-term counts, Bloom bit-setting.
+constexpr uint32_t BUILD_CHUNK = 16384;  // positions per CTA
+constexpr uint32_t BUILD_THREADS = 256;
+struct CountArgs {
+    const uint8_t *docs;
+    const uint64_t *doc_off;
+    const uint32_t *chunk_doc;     // per CTA: document
+    const uint64_t *chunk_p0;      // per CTA: first window position
+    const uint64_t *table_base;    // per document (in slots), relative to `tables`
+    const uint32_t *table_cap;     // per document: set_slots(windows)
+    unsigned long long *tables;
+    unsigned long long *v;         // out: distinct terms per document (zeroed before)
+    uint32_t *has_empty;           // per document flag for the EMPTY code (bytes kind)
+    uint32_t kind, k;
+};
+void launch_doc_count(const CountArgs &a, uint32_t n_chunks, cudaStream_t s);
+
+struct SetBitsArgs {
+    const uint8_t *docs;
+    const uint64_t *doc_off;
+    const uint32_t *chunk_doc;
+    const uint64_t *chunk_p0;
+    const uint32_t *doc_block;     // per original document: block
+    const uint32_t *doc_col;       // per original document: column within the block
+    const DevBlock *blocks;
+    uint32_t *rows32;
+    uint32_t kind, k, h;
+};
+void launch_doc_setbits(const SetBitsArgs &a, uint32_t n_chunks, cudaStream_t s);
+
+}  // namespace cobs

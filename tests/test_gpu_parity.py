@@ -1,0 +1,192 @@
+"""CUDA path vs CPU oracle, element by element, through the C ABI.
+
+Bit-exact: index bytes, block table and permutation; per query the distinct
+term count, the threshold, and the sorted (document id, score) hit list.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_1905_09624_gb300 import cobs
+
+from parity import assert_index_equal, assert_results_equal, device_index, oracle_index, small_compact
+
+pytestmark = pytest.mark.gpu
+
+FORMS = [cobs.COBS_PLAIN, cobs.COBS_BATCHED, cobs.COBS_GRAPH]
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    wl = synth.config1()
+    return wl, oracle_index(wl), device_index(wl)
+
+
+def test_cfg1_index_bit_exact(cfg1):
+    wl, ref, dix = cfg1
+    assert_index_equal(dix, ref)
+
+
+@pytest.mark.parametrize("flags", FORMS)
+def test_cfg1_results_all_forms(cfg1, flags):
+    wl, ref, dix = cfg1
+    got = dix.query(wl.queries, wl.q_off, wl.thresholds, flags)
+    assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
+    # every exact substring query finds its source document with score l
+    for i in range(100):
+        assert wl.src[i] in got[i][2].tolist()
+
+
+@pytest.fixture(scope="module")
+def compact():
+    wl = small_compact()
+    return wl, oracle_index(wl), device_index(wl)
+
+
+def test_compact_index_bit_exact(compact):
+    wl, ref, dix = compact
+    assert len(ref.blocks()) == 3 and ref.blocks()[-1]["n_docs"] == 600 - 512
+    assert_index_equal(dix, ref)
+
+
+@pytest.mark.parametrize("slice_bytes", [32, 64, 128])
+def test_compact_batched_slice_widths(compact, slice_bytes):
+    wl, ref, dix = compact
+    eng = cobs.Engine(dix, slice_bytes=slice_bytes)
+    got = eng.query_host(wl.queries, wl.q_off, wl.thresholds, cobs.COBS_BATCHED)
+    assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
+
+
+@pytest.mark.parametrize("flags", FORMS)
+def test_compact_forms(compact, flags):
+    wl, ref, dix = compact
+    got = dix.query(wl.queries, wl.q_off, wl.thresholds, flags)
+    assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
+
+
+def test_many_hits_large_segments():
+    # K = 1 permille: every document with one matching term is a hit, so hit lists
+    # exceed the shared-memory sort and use the global merge passes.
+    wl = small_compact(seed=37, n_docs=2500, median=2000, block_docs=1024, n_q=30)
+    ref = oracle_index(wl)
+    dix = device_index(wl)
+    thr = np.full(wl.n_queries, 1, np.uint16)
+    got = dix.query(wl.queries, wl.q_off, thr, cobs.COBS_BATCHED)
+    assert max(len(g[2]) for g in got) > 1024
+    assert_results_equal(got, ref, wl.query_list(), thr, which=range(0, wl.n_queries, 7))
+
+
+def test_hit_capacity_overflow_reruns(compact):
+    wl, ref, dix = compact
+    eng = cobs.Engine(dix, max_hits=4)
+    thr = np.full(wl.n_queries, 1, np.uint16)
+    got = eng.query_host(wl.queries, wl.q_off, thr, cobs.COBS_BATCHED)
+    assert_results_equal(got, ref, wl.query_list(), thr, which=range(0, wl.n_queries, 11))
+
+
+def test_uneven_query_lengths_counter_classes():
+    # Queries from 0 bytes to 20 kb: empty and shorter-than-k queries (l = 0),
+    # lengths spanning the 8-, 12- and 16-level counter kernels, spilled
+    # distinct-term sets (> 2048 windows), and windows with non-ACGT bytes.
+    lens = synth.lognormal_lengths(91, 80, 30000, 0.4, 25000, 90000)
+    docs, off = synth.dna_docs(91, lens)
+    qb, qo, src = synth.dna_queries(92, 60, docs, off, n_tp=40, median=2000, sigma=1.5, lo=1, hi=20000,
+                                    rate_lo=0.0, rate_hi=0.05)
+    ql = [bytes(qb[qo[i]:qo[i + 1]]) for i in range(60)]
+    ql[3] = b""
+    ql[4] = b"ACGT" * 7          # 28 < k
+    ql[5] = ql[5][:200] + b"NNNN" + ql[5][200:] if len(ql[5]) > 300 else b"ACGTN" * 80
+    ql[6] = ql[6].lower()        # no valid windows
+    qo2 = np.zeros(61, np.uint64)
+    qo2[1:] = np.cumsum([len(x) for x in ql])
+    qb2 = np.frombuffer(b"".join(ql), np.uint8)
+    thr = synth.choice_u16(93, 60, [500, 700, 900, 1000])
+    wl = synth.Workload("uneven", 0, 31, 1, 0.3, 32, 32, docs, off, qb2, qo2, thr, src)
+    ref = oracle_index(wl)
+    dix = device_index(wl)
+    assert_index_equal(dix, ref)
+    for flags in FORMS:
+        got = dix.query(wl.queries, wl.q_off, thr, flags)
+        assert_results_equal(got, ref, ql, thr)
+        assert got[3][0] == 0 and len(got[3][2]) == 0
+
+
+@pytest.mark.parametrize("kind,q", [(1, 31), (0, 15), (1, 32), (0, 1)])
+def test_dna_kinds_and_lengths(kind, q):
+    wl = small_compact(seed=17, n_docs=150, median=1500, block_docs=64, n_q=50, q_len=120, kind=kind, q=q)
+    ref = oracle_index(wl)
+    dix = device_index(wl)
+    assert_index_equal(dix, ref)
+    got = dix.query(wl.queries, wl.q_off, wl.thresholds, cobs.COBS_BATCHED)
+    assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
+
+
+@pytest.mark.parametrize("q,h", [(8, 3), (5, 2), (3, 1)])
+def test_text_qgrams_multi_hash(q, h):
+    wl = synth.config4(n_docs=400, n_q=120, n_words=3000, median=3000, lo=50, hi=20000, block_docs=128)
+    wl.q, wl.num_hashes = q, h
+    ref = oracle_index(wl)
+    dix = device_index(wl)
+    assert_index_equal(dix, ref)
+    for flags in FORMS:
+        got = dix.query(wl.queries, wl.q_off, wl.thresholds, flags)
+        assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
+
+
+def test_classic_equals_compact_single_block():
+    wl = small_compact(seed=23, n_docs=90, block_docs=0, n_q=40)
+    ref = oracle_index(wl)
+    dix_c = device_index(wl)
+    wl.block_docs = 128
+    dix_k = device_index(wl)
+    a = dix_c.query(wl.queries, wl.q_off, wl.thresholds)
+    b = dix_k.query(wl.queries, wl.q_off, wl.thresholds)
+    assert_results_equal(a, ref, wl.query_list(), wl.thresholds)
+    for x, y in zip(a, b):
+        assert x[0] == y[0] and x[1] == y[1] and np.array_equal(x[2], y[2]) and np.array_equal(x[3], y[3])
+
+
+def test_save_load_roundtrip(compact, tmp_path):
+    wl, ref, dix = compact
+    hix = dix.download()
+    p = str(tmp_path / "i.cobs")
+    hix.save(p)
+    dix2 = cobs.DeviceIndex.load(cobs.HostIndex.load(p))
+    assert_index_equal(dix2, ref)
+    got = dix2.query(wl.queries, wl.q_off, wl.thresholds)
+    assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
+
+
+def test_errors():
+    wl = small_compact(seed=29, n_docs=20, n_q=4, score_bits=16)
+    dix = device_index(wl)
+    thr = np.array([0, 500, 500, 500], np.uint16)
+    with pytest.raises(cobs.CobsError) as e:
+        dix.query(wl.queries, wl.q_off, thr)
+    assert e.value.status == cobs.COBS_ERR_ARG
+    big = np.frombuffer(b"A" * 70000, np.uint8)
+    with pytest.raises(cobs.CobsError) as e:
+        dix.query(big, np.array([0, 70000], np.uint64), np.array([500], np.uint16))
+    assert e.value.status == cobs.COBS_ERR_OVERFLOW
+    res = dix.query(np.zeros(0, np.uint8), np.zeros(1, np.uint64), np.zeros(0, np.uint16))
+    assert res == []
+
+
+def test_empty_and_tiny_documents():
+    docs = [b"", b"ACG", b"ACGTACGTACGTACGTACGTACGTACGTACGTAC", b"N" * 50, b"GATTACA" * 10]
+    off = np.zeros(len(docs) + 1, np.uint64)
+    off[1:] = np.cumsum([len(d) for d in docs])
+    db = np.frombuffer(b"".join(docs), np.uint8)
+    qs = [b"GATTACAGATTACAGATTACAGATTACAGATTACA", b"ACGTACGTACGTACGTACGTACGTACGTACGTA", b"TTTT"]
+    qo = np.zeros(4, np.uint64)
+    qo[1:] = np.cumsum([len(x) for x in qs])
+    qb = np.frombuffer(b"".join(qs), np.uint8)
+    thr = np.array([1000, 500, 1000], np.uint16)
+    for B in (0, 2):
+        wl = synth.Workload("tiny", 0, 31, 1, 0.3, B, 32, db, off, qb, qo, thr, np.full(3, -1))
+        ref = oracle_index(wl)
+        dix = device_index(wl)
+        assert_index_equal(dix, ref)
+        for flags in FORMS:
+            assert_results_equal(dix.query(qb, qo, thr, flags), ref, qs, thr)
