@@ -1,0 +1,423 @@
+"""Benchmark of the COBS query path on GB300.
+
+A step = one pass of the whole query path (distinct terms + hashes + row
+indices, gather/AND/ADD with the fused threshold, hit compaction and sort) over
+one batch of queries, with the index and the queries resident in HBM.
+
+Default workload: the compact 10,000-document index (log-normal lengths,
+median 100 kb), 10,000 queries of 1,000 bases with 1% substitutions, k = 31
+canonical, h = 1, p = 0.3, blocks of 8,192, thresholds 0.5 / 0.8 / 1.0
+(query i gets the (i mod 3)-th).  Inputs are seeded synthetic data.
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "query k-mers/s (batched form, index and queries resident in HBM)"
+UNIT = "k-mers/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def workload(name):
+    import synth
+    if name == "cfg1":
+        return synth.config1()
+    if name == "cfg2":
+        return synth.config2()
+    if name == "cfg3":
+        return synth.config3()
+    if name == "cfg4":
+        return synth.config4()
+    if name == "cfg2-small":
+        return synth.config2(n_docs=2000, n_q=2000)
+    raise ValueError(name)
+
+
+def describe(wl, name):
+    lens = np.diff(wl.q_off)
+    return {"workload": f"{name}: {wl.name}", "n_docs": wl.n_docs, "doc_bytes": int(wl.doc_off[-1]),
+            "n_queries": wl.n_queries, "query_bytes": int(wl.q_off[-1]),
+            "query_len_min": int(lens.min()), "query_len_max": int(lens.max()),
+            "term_kind": wl.term_kind, "q": wl.q, "num_hashes": wl.num_hashes, "fpr": wl.fpr,
+            "block_docs": wl.block_docs, "score_bits": wl.score_bits,
+            "thresholds_permille": sorted(set(int(t) for t in wl.thresholds))}
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append((time.time(), ln.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        sm, mx, reasons = [], 0.0, set()
+        for t, ln in self.lines:
+            if not (t0 - 0.25 <= t <= t1 + 0.25):
+                continue
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 10:
+                continue
+            try:
+                sm.append(float(p[2]))
+                mx = max(mx, float(p[3]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for nm, v in zip(names, p[6:10]):
+                if v.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_record(kernel_src):
+    """DRAM bytes per launch of the gather kernel from the committed ncu summary,
+    or None when the kernel source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "gather_batched_cfg2_dram.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for ln in open(p):
+        if "=" in ln and not ln.startswith("#"):
+            k, v = ln.split("=", 1)
+            kv[k.strip()] = v.strip()
+    digest = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    if kv.get("gather_cu_sha256_16") != digest:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_baseline(wl, sample_queries, budget_s=20.0, nthreads=None):
+    """The oracle as it stands: its index built with the oracle functions on
+    disjoint document ranges (threads, untimed), then single-threaded queries of
+    a bounded sample timed."""
+    import oracle
+    t0 = time.perf_counter()
+    ix = oracle.build_index_threaded(oracle.make_params(**wl.params()), wl.docs, wl.doc_off, nthreads)
+    t_setup = time.perf_counter() - t0
+    ql = wl.query_list()
+    terms, n, t = 0, 0, 0.0
+    for i in sample_queries:
+        s = time.perf_counter()
+        ell, _, _, _ = ix.query(ql[i], int(wl.thresholds[i]))
+        t += time.perf_counter() - s
+        terms += ell
+        n += 1
+        if t > budget_s:
+            break
+    return ix, {"value": terms / t if t else None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"{n} queries of the workload (first {n} of a seeded sample), single thread; "
+                          f"oracle index built untimed in {t_setup:.1f} s",
+                "seconds": t, "terms": terms}
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    wl = workload(args.config)
+    import oracle
+    ix = oracle.build_index_threaded(oracle.make_params(**wl.params()), wl.docs, wl.doc_off)
+    ql = wl.query_list()
+    rng = np.random.default_rng(12345)
+    order = rng.permutation(wl.n_queries)
+    per_step = max(1, args.ref_queries_per_step)
+    pos = 0
+    step_times, step_terms = [], []
+    for s in range(args.warmup + args.steps):
+        idx = [int(order[(pos + j) % wl.n_queries]) for j in range(per_step)]
+        pos += per_step
+        t0 = time.perf_counter()
+        terms = 0
+        for i in idx:
+            terms += ix.query(ql[i], int(wl.thresholds[i]))[0]
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            step_times.append(dt)
+            step_terms.append(terms)
+    T = sum(step_times)
+    value = sum(step_terms) / T
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / len(step_times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+           "data": "synthetic", "config": describe(wl, args.config),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{per_step} queries per step, single thread, oracle index built untimed"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------- GPU
+def run_gpu(args):
+    import torch
+    from paper_1905_09624_gb300 import cobs
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the CUDA library has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    wl = workload(args.config)
+    L = cobs.lib()
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+
+    # ---- device build (documents already in HBM), and with the H2D copy
+    P = cobs.make_params(**wl.params())
+    d_docs = torch.from_numpy(wl.docs).to("cuda")
+    d_doff = torch.from_numpy(wl.doc_off.view(np.int64)).to("cuda")
+    torch.cuda.synchronize()
+    build_ms = []
+    dix = None
+    for rep in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            dix = cobs.DeviceIndex.build_resident(P, d_docs, d_doff, wl.doc_off, stream=sh)
+            e1.record(stream)
+        e1.synchronize()
+        build_ms.append(e0.elapsed_time(e1))
+    t0 = time.perf_counter()
+    dix_h2d = cobs.DeviceIndex.build(P, wl.docs, wl.doc_off, device=local)
+    build_h2d_s = time.perf_counter() - t0
+    del dix_h2d, d_docs, d_doff
+    info = dix.info()
+    rows_per_term = sum(b["rowbytes"] for b in info["blocks"]) * wl.num_hashes
+
+    # ---- queries resident in HBM
+    d_q = torch.from_numpy(wl.queries).to("cuda")
+    d_off = torch.from_numpy(wl.q_off.view(np.int64)).to("cuda")
+    d_thr = torch.from_numpy(wl.thresholds.view(np.int16)).to("cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    eng = cobs.Engine(dix, stream=sh, slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm)
+    tuned = None
+    if args.autotune:
+        tuned = eng.autotune(d_q, d_off, wl.q_off, d_thr)
+
+    def step(flags):
+        eng.query_device(d_q, d_off, wl.q_off, d_thr, flags)
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(rank + 1)
+
+    form = cobs.COBS_GRAPH if args.form == "graph" else cobs.COBS_BATCHED
+    for _ in range(args.warmup):
+        flush_l2()
+        step(form)
+        eng.stats()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    gather_ms, launches, terms_total, row_bytes_total = [], 0, 0, 0
+    t_wall0 = time.time()
+    for i in range(args.steps):
+        flush_l2()
+        ev[i][0].record(stream)
+        step(form)
+        ev[i][1].record(stream)
+        st = eng.stats()  # synchronises this step
+        gather_ms.append(st["ms_gather"])
+        launches += st["launches"]
+        terms_total += st["terms"]
+        row_bytes_total += st["row_bytes"]
+    stream.synchronize()
+    barrier()
+    t_wall1 = time.time()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    T = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([T], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        T = float(t.item())
+        u = torch.tensor([terms_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        terms_all = float(u.item())
+    else:
+        terms_all = float(terms_total)
+    value = terms_all / T
+
+    phases = {k: st[k] for k in ("ms_terms", "ms_gather", "ms_hits", "ms_total")}
+    # ---- results of the timed form, kept for the plain comparison
+    batched_res = eng.download_arrays()
+
+    # ---- end to end through the public host-buffer API (H2D + query + D2H)
+    e2e_times = []
+    h2d = int(wl.q_off[-1]) + wl.q_off.nbytes + wl.thresholds.nbytes
+    d2h = 0
+    for i in range(max(2, args.e2e_steps) + 1):
+        t0 = time.perf_counter()
+        res = eng.query_host_arrays(wl.queries, wl.q_off, wl.thresholds, form)
+        dt = time.perf_counter() - t0
+        if i:
+            e2e_times.append(dt)
+        # per query: terms, threshold, hit offset; per hit: id, score
+        d2h = wl.n_queries * 4 * 2 + (wl.n_queries + 1) * 8 + len(res[3]) * 8
+    e2e_value = terms_total / args.steps / float(np.mean(e2e_times))
+
+    # ---- plain form (one query per kernel sequence) on the same batch
+    plain = None
+    if not args.skip_plain:
+        pr = []
+        for rep in range(2):
+            flush_l2()
+            step(cobs.COBS_PLAIN)
+            pr.append(eng.stats())
+        plain_res = eng.download_arrays()
+        same = all(np.array_equal(a, b) for a, b in zip(plain_res, batched_res))
+        pt = min(p["ms_total"] for p in pr) / 1e3
+        plain = {"value": pr[0]["terms"] / pt, "unit": UNIT, "ms": pt * 1e3,
+                 "row_gbs_logical": pr[0]["row_bytes"] / pt / 1e9,
+                 "launches": pr[0]["launches"], "results_identical_to_batched": bool(same)}
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+
+    peak, peak_kind = measured_peaks()
+    g_ms = float(np.mean(gather_ms))
+    alg_bytes = row_bytes_total / args.steps
+    achieved = alg_bytes / (g_ms / 1e3) / 1e9 if g_ms > 0 else None
+    traffic = traffic_record(os.path.join(ROOT, "paper_1905_09624_gb300", "csrc", "gather.cu"))
+    roofline = {"bound": "hbm", "kernel": "k_gather_batched", "achieved": achieved, "peak": peak,
+                "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback", "unit": "GB/s", "frac": achieved / peak if achieved else None,
+                "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
+                "launch_ms": g_ms, "bytes_rule": "sum over distinct query terms and blocks of h * rowbytes_b"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded)",
+           "config": dict(describe(wl, args.config), form=args.form,
+                          l2="flushed between steps (512 MB write outside the timed events)",
+                          parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
+                          slice_bytes=eng.stats()["slice_bytes"], ctas_per_sm=eng.stats()["ctas_per_sm"],
+                          autotuned=tuned),
+           "row_gbs_logical": row_bytes_total / T / 1e9,
+           "roofline": roofline,
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "ms_per_step": 1e3 * float(np.mean(e2e_times))},
+           "gpu_launches": launches, "clocks": clocks, "phases_ms_last_step": phases, "plain": plain,
+           "build": {"ms_device": min(build_ms), "input_bytes": int(wl.doc_off[-1]),
+                     "gbs_device": int(wl.doc_off[-1]) / (min(build_ms) / 1e3) / 1e9,
+                     "gbs_with_h2d": int(wl.doc_off[-1]) / build_h2d_s / 1e9,
+                     "index_bytes": info["rows_bytes"], "blocks": len(info["blocks"])},
+           "speedup_batched_over_plain": (value / plain["value"]) if plain else None}
+    if plain:
+        out["plain"]["frac_of_hbm_peak"] = plain["row_gbs_logical"] / peak
+
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        rng = np.random.default_rng(777)
+        sample = rng.permutation(wl.n_queries)[:args.cpu_queries].tolist()
+        _, cpu = oracle_baseline(wl, sample, budget_s=args.cpu_budget_s)
+        out["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--config", default="cfg2")
+    ap.add_argument("--form", default="batched", choices=["batched", "graph"])
+    ap.add_argument("--slice-bytes", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-queries", type=int, default=400)
+    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    ap.add_argument("--ref-queries-per-step", type=int, default=40)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -90,6 +90,9 @@ typedef struct cobs_hits {
     const uint32_t *scores;   /* score of each hit (number of terms present) */
 } cobs_hits;
 
+/* The hit lists of all queries of one result are stored back to back in query
+ * order: hits[i].doc_ids == hits[0].doc_ids + (hits of queries 0..i-1), and the
+ * same for scores, so a caller can copy them in one piece. */
 typedef struct cobs_result {
     uint64_t n_queries;
     const cobs_hits *hits;    /* hits[i] for query i; storage owned by the result */

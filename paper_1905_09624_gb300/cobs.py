@@ -178,6 +178,37 @@ def result_to_python(res_ptr):
     return out
 
 
+_HITS_DT = np.dtype([("n_terms", "<u4"), ("min_score", "<u4"), ("n_hits", "<u4"), ("_pad", "<u4"),
+                     ("doc_ids", "<u8"), ("scores", "<u8")])
+
+
+def result_to_arrays(res_ptr):
+    """Copy a cobs_result into flat arrays (n_terms, min_score, hit_offsets[n+1],
+    ids, scores) and free it.  The hits of all queries are contiguous in query
+    order inside a result, so two copies suffice."""
+    res = res_ptr.contents
+    n = res.n_queries
+    if n == 0:
+        lib().cobs_result_free(res_ptr)
+        z = np.zeros(0, np.uint32)
+        return z, z, np.zeros(1, np.uint64), z, z
+    raw = (ctypes.c_char * (32 * n)).from_address(ctypes.addressof(res.hits.contents))
+    h = np.frombuffer(raw, dtype=_HITS_DT).copy()
+    off = np.zeros(n + 1, np.uint64)
+    np.cumsum(h["n_hits"], out=off[1:])
+    total = int(off[-1])
+    if total:
+        first = int(np.argmax(h["n_hits"] > 0))
+        base_ids = int(h["doc_ids"][first]) - 4 * int(off[first])
+        base_sc = int(h["scores"][first]) - 4 * int(off[first])
+        ids = np.frombuffer((ctypes.c_char * (4 * total)).from_address(base_ids), np.uint32).copy()
+        sc = np.frombuffer((ctypes.c_char * (4 * total)).from_address(base_sc), np.uint32).copy()
+    else:
+        ids = sc = np.zeros(0, np.uint32)
+    lib().cobs_result_free(res_ptr)
+    return h["n_terms"].copy(), h["min_score"].copy(), off, ids, sc
+
+
 class HostIndex:
     """cobs_index (host copy)."""
 
@@ -306,10 +337,22 @@ class Engine:
                                            ctypes.byref(res)), "cobs_engine_query_host")
         return result_to_python(res)
 
+    def query_host_arrays(self, queries, q_off, thr, flags=COBS_BATCHED):
+        """cobs_engine_query_host, results as flat arrays (see result_to_arrays)."""
+        res = ctypes.POINTER(cobs_result)()
+        check(lib().cobs_engine_query_host(self.h, _ptr(queries), _ptr(q_off), _ptr(thr), len(q_off) - 1, flags,
+                                           ctypes.byref(res)), "cobs_engine_query_host")
+        return result_to_arrays(res)
+
     def download(self):
         res = ctypes.POINTER(cobs_result)()
         check(lib().cobs_engine_download(self.h, ctypes.byref(res)), "cobs_engine_download")
         return result_to_python(res)
+
+    def download_arrays(self):
+        res = ctypes.POINTER(cobs_result)()
+        check(lib().cobs_engine_download(self.h, ctypes.byref(res)), "cobs_engine_download")
+        return result_to_arrays(res)
 
     def results_device(self):
         ptrs = [vp() for _ in range(5)]

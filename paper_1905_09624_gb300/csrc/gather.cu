@@ -135,20 +135,11 @@ __device__ __forceinline__ void accumulate(uint32_t (&lv)[4][L], const uint8_t *
     }
 }
 
-// One warp-tile: QPW queries x one row slice of one block.
-template <int LPQ, int G, int L>
-__device__ __forceinline__ void tile_body(const GatherArgs &a, const DevBlock &blk, uint32_t block_idx,
-                                          uint32_t col, bool active, uint32_t q, uint32_t ell) {
-    uint32_t lv[4][L];
-#pragma unroll
-    for (int w = 0; w < 4; w++)
-#pragma unroll
-        for (int l = 0; l < L; l++) lv[w][l] = 0u;
-    const uint32_t n = active ? ell : 0u;
-    const uint32_t *ridx = a.rows_idx + (uint64_t)(block_idx * a.h) * a.tcap + a.term_base[q];
-    const uint8_t *colbase = a.rows + blk.row_offset + col;
-    accumulate<L, G>(lv, colbase, blk.rowbytes, ridx, a.tcap, a.h, 0u, n);
-    if (n == 0u) return;
+// Threshold (Sec. 2.1: score >= ceil(K l)) and hit emission of one lane's 128
+// documents after all terms of its query were added.
+template <int L>
+__device__ __forceinline__ void emit_hits(const GatherArgs &a, const DevBlock &blk, uint32_t col, uint32_t q,
+                                          uint32_t ell, const uint32_t (&lv)[4][L]) {
     const uint32_t mn = (uint32_t)(((uint64_t)a.thr[q] * ell + 999u) / 1000u);
     const uint32_t doc0 = col * 8u;
     uint32_t ge[4];
@@ -182,6 +173,23 @@ __device__ __forceinline__ void tile_body(const GatherArgs &a, const DevBlock &b
     }
 }
 
+// One warp-tile of the register kernel: QPW queries x one row slice of one block.
+template <int LPQ, int G, int L>
+__device__ __forceinline__ void tile_body(const GatherArgs &a, const DevBlock &blk, uint32_t block_idx,
+                                          uint32_t col, bool active, uint32_t q, uint32_t ell) {
+    uint32_t lv[4][L];
+#pragma unroll
+    for (int w = 0; w < 4; w++)
+#pragma unroll
+        for (int l = 0; l < L; l++) lv[w][l] = 0u;
+    const uint32_t n = active ? ell : 0u;
+    const uint32_t *ridx = a.rows_idx + (uint64_t)(block_idx * a.h) * a.tcap + a.term_base[q];
+    const uint8_t *colbase = a.rows + blk.row_offset + col;
+    accumulate<L, G>(lv, colbase, blk.rowbytes, ridx, a.tcap, a.h, 0u, n);
+    if (n == 0u) return;
+    emit_hits<L>(a, blk, col, q, ell, lv);
+}
+
 // Persistent batched kernel.  Tiles are (row slice, group of QPW queries), slice
 // major, so the CTAs resident at any moment read the same few slices and the
 // slices stay in L2; within a slice the groups run longest query first.
@@ -211,6 +219,172 @@ __global__ void __launch_bounds__(GATHER_THREADS) k_gather_batched(GatherArgs a)
     }
 }
 
+// ------------------------------------------------------- cp.async pipeline
+// h == 1 form of the batched kernel: every lane streams its query's row slices
+// through a ring of PIPE_D stages of PIPE_G rows in shared memory (cp.async,
+// 16 bytes per lane and row, L2 only), so up to PIPE_D - 1 groups of loads are
+// in flight while the adder tree consumes the oldest group.  Row indices are
+// prefetched two groups ahead in registers.
+constexpr int PIPE_WARPS = 2;
+constexpr int PIPE_THREADS = PIPE_WARPS * 32;
+constexpr int PIPE_G = 16;
+constexpr int PIPE_D = 3;
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, uint32_t src_bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+struct W4 {
+    uint32_t v[4];
+};
+__device__ __forceinline__ W4 w4(const uint4 &u) {
+    W4 r;
+    r.v[0] = u.x; r.v[1] = u.y; r.v[2] = u.z; r.v[3] = u.w;
+    return r;
+}
+// full adder of two words into level LV of all four counters; returns the carry
+template <int LV, int L>
+__device__ __forceinline__ W4 csa_lv(uint32_t (&lv)[4][L], const W4 &a, const W4 &b) {
+    W4 hi;
+#pragma unroll
+    for (int w = 0; w < 4; w++) csa(hi.v[w], lv[w][LV], lv[w][LV], a.v[w], b.v[w]);
+    return hi;
+}
+template <int FROM, int L>
+__device__ __forceinline__ void ripple(uint32_t (&lv)[4][L], W4 c) {
+#pragma unroll
+    for (int w = 0; w < 4; w++)
+#pragma unroll
+        for (int l = FROM; l < L; l++) {
+            uint32_t t = lv[w][l] & c.v[w];
+            lv[w][l] ^= c.v[w];
+            c.v[w] = t;
+        }
+}
+// Harley-Seal tree over the 16 rows of one stage (stride 32 uint4 = one per lane).
+template <int L>
+__device__ __forceinline__ void hs16_stage(uint32_t (&lv)[4][L], const uint4 *st) {
+    W4 tA = csa_lv<0>(lv, w4(st[0 * 32]), w4(st[1 * 32]));
+    W4 tB = csa_lv<0>(lv, w4(st[2 * 32]), w4(st[3 * 32]));
+    W4 fA = csa_lv<1>(lv, tA, tB);
+    tA = csa_lv<0>(lv, w4(st[4 * 32]), w4(st[5 * 32]));
+    tB = csa_lv<0>(lv, w4(st[6 * 32]), w4(st[7 * 32]));
+    W4 fB = csa_lv<1>(lv, tA, tB);
+    W4 eA = csa_lv<2>(lv, fA, fB);
+    tA = csa_lv<0>(lv, w4(st[8 * 32]), w4(st[9 * 32]));
+    tB = csa_lv<0>(lv, w4(st[10 * 32]), w4(st[11 * 32]));
+    fA = csa_lv<1>(lv, tA, tB);
+    tA = csa_lv<0>(lv, w4(st[12 * 32]), w4(st[13 * 32]));
+    tB = csa_lv<0>(lv, w4(st[14 * 32]), w4(st[15 * 32]));
+    fB = csa_lv<1>(lv, tA, tB);
+    W4 eB = csa_lv<2>(lv, fA, fB);
+    W4 six = csa_lv<3>(lv, eA, eB);
+    ripple<4, L>(lv, six);
+}
+
+__device__ __forceinline__ void load_idx16(const uint32_t *ridx, uint32_t g, uint32_t ng, uint32_t (&r)[16]) {
+    if (g < ng) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) {
+            uint4 v = __ldg(reinterpret_cast<const uint4 *>(ridx + g * 16u + j));
+            r[j] = v.x; r[j + 1] = v.y; r[j + 2] = v.z; r[j + 3] = v.w;
+        }
+    }
+}
+
+__device__ __forceinline__ void issue16(uint4 *stage_lane, const uint8_t *colbase, uint32_t rowbytes,
+                                        const uint32_t (&r)[16], uint32_t t0, uint32_t n) {
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+        const bool ok = t0 + j < n;
+        const uint8_t *src = ok ? colbase + (uint64_t)r[j] * rowbytes : colbase;
+        cp_async16(stage_lane + j * 32, src, ok ? 16u : 0u);
+    }
+}
+
+template <int LPQ, int L>
+__global__ void __launch_bounds__(PIPE_THREADS) k_gather_pipe(GatherArgs a) {
+    __shared__ __align__(16) uint4 s_stage[PIPE_WARPS][PIPE_D][PIPE_G][32];
+    constexpr uint32_t QPW = 32 / LPQ;
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t qslot = lane / LPQ;
+    const uint32_t c = lane % LPQ;
+    const unsigned long long n_tiles = (unsigned long long)a.n_slices * a.n_groups;
+    for (;;) {
+        unsigned long long tile = 0;
+        if (lane == 0) tile = atomicAdd(a.work_counter, 1ULL);
+        tile = __shfl_sync(FULL, tile, 0);
+        if (tile >= n_tiles) break;
+        const uint32_t s = (uint32_t)(tile / a.n_groups);
+        const uint32_t g0 = (uint32_t)(tile % a.n_groups);
+        const SliceDesc sd = a.slices[s];
+        const DevBlock blk = a.blocks[sd.block];
+        const uint32_t qi = g0 * QPW + qslot;
+        const bool valid = qi < a.n_queries;
+        const uint32_t q = valid ? a.order[qi] : 0u;
+        const uint32_t ell = valid ? a.ell[q] : 0u;
+        const uint32_t col = sd.byte_off + c * 16u;
+        const bool active = valid && col < blk.rowbytes;
+        const uint32_t n = active ? ell : 0u;
+        const uint32_t ng = (n + 15u) >> 4;
+        const uint32_t *ridx = a.rows_idx + (uint64_t)sd.block * a.tcap + a.term_base[q];
+        const uint8_t *colbase = a.rows + blk.row_offset + col;
+        const uint32_t rowbytes = blk.rowbytes;
+
+        uint32_t lv[4][L];
+#pragma unroll
+        for (int w = 0; w < 4; w++)
+#pragma unroll
+            for (int l = 0; l < L; l++) lv[w][l] = 0u;
+        uint32_t ra[16], rb[16];
+        load_idx16(ridx, 0, ng, ra);
+        load_idx16(ridx, 1, ng, rb);
+        uint32_t gi = 0, si = 0;  // next group to issue, its stage
+#pragma unroll
+        for (int p = 0; p < PIPE_D - 1; p++) {
+            if (gi < ng) issue16(&s_stage[warp][si][0][lane], colbase, rowbytes, ra, gi * 16u, n);
+            cp_async_commit();
+            gi++;
+            si = si + 1 == PIPE_D ? 0 : si + 1;
+#pragma unroll
+            for (int j = 0; j < 16; j++) ra[j] = rb[j];
+            load_idx16(ridx, gi + 1, ng, rb);
+        }
+        uint32_t sc = 0;  // stage being consumed
+        for (uint32_t g = 0; g < ng; g++) {
+            if (gi < ng) issue16(&s_stage[warp][si][0][lane], colbase, rowbytes, ra, gi * 16u, n);
+            cp_async_commit();
+            gi++;
+            si = si + 1 == PIPE_D ? 0 : si + 1;
+#pragma unroll
+            for (int j = 0; j < 16; j++) ra[j] = rb[j];
+            load_idx16(ridx, gi + 1, ng, rb);
+            cp_async_wait<PIPE_D - 1>();
+            hs16_stage<L>(lv, &s_stage[warp][sc][0][lane]);
+            sc = sc + 1 == PIPE_D ? 0 : sc + 1;
+        }
+        cp_async_wait<0>();
+        if (n) emit_hits<L>(a, blk, col, q, ell, lv);
+    }
+}
+
+template <int LPQ>
+static void launch_pipe_L(const GatherArgs &a, uint32_t L, uint32_t grid, cudaStream_t s) {
+    switch (L) {
+        case 8: k_gather_pipe<LPQ, 8><<<grid, PIPE_THREADS, 0, s>>>(a); break;
+        case 12: k_gather_pipe<LPQ, 12><<<grid, PIPE_THREADS, 0, s>>>(a); break;
+        case 16: k_gather_pipe<LPQ, 16><<<grid, PIPE_THREADS, 0, s>>>(a); break;
+        default: k_gather_pipe<LPQ, 24><<<grid, PIPE_THREADS, 0, s>>>(a); break;
+    }
+}
+
 template <int LPQ, int G>
 static void launch_L(const GatherArgs &a, uint32_t L, uint32_t grid, cudaStream_t s) {
     switch (L) {
@@ -232,17 +406,27 @@ uint32_t counter_levels_for(uint32_t max_terms) {
 
 void launch_gather_batched_L(const GatherArgs &a, uint32_t lanes_per_query, uint32_t L, uint32_t grid,
                              cudaStream_t s) {
-    const bool g16 = a.h == 1;
+    if (a.h == 1) {
+        // cp.async pipeline
+        switch (lanes_per_query) {
+            case 2: launch_pipe_L<2>(a, L, grid, s); break;
+            case 4: launch_pipe_L<4>(a, L, grid, s); break;
+            default: launch_pipe_L<8>(a, L, grid, s); break;
+        }
+        return;
+    }
     switch (lanes_per_query) {
-        case 2: g16 ? launch_L<2, 16>(a, L, grid, s) : launch_L<2, 8>(a, L, grid, s); break;
-        case 4: g16 ? launch_L<4, 16>(a, L, grid, s) : launch_L<4, 8>(a, L, grid, s); break;
-        default: g16 ? launch_L<8, 16>(a, L, grid, s) : launch_L<8, 8>(a, L, grid, s); break;
+        case 2: launch_L<2, 8>(a, L, grid, s); break;
+        case 4: launch_L<4, 8>(a, L, grid, s); break;
+        default: launch_L<8, 8>(a, L, grid, s); break;
     }
 }
 
+// Resident CTAs per SM of the batched kernel used for h hashes (persistent grid
+// = SMs x this).
 int gather_batched_max_blocks_per_sm(uint32_t lanes_per_query, uint32_t h) {
     int nb = 0;
-    if (h == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gather_batched<8, 16, 12>, GATHER_THREADS, 0);
+    if (h == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gather_pipe<8, 12>, PIPE_THREADS, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gather_batched<8, 8, 12>, GATHER_THREADS, 0);
     (void)lanes_per_query;
     return nb;

@@ -828,11 +828,17 @@ cobs_status engine_query(cobs_engine *eng, const uint8_t *d_bytes, const uint64_
                 return set_error(COBS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
             }
             eng->gsig = sig;
+            eng->graph_stats[0] = eng->stat_launches;
+            eng->graph_stats[1] = eng->stat_gather_launches;
+            eng->graph_stats[2] = eng->stat_tiles;
         }
         CU(cudaEventRecord(eng->ev[0], eng->stream));
         CU(cudaGraphLaunch(eng->gexec, eng->stream));
         CU(cudaEventRecord(eng->ev[3], eng->stream));
-        eng->stat_launches = 1;
+        // kernels inside the graph
+        eng->stat_launches = eng->graph_stats[0];
+        eng->stat_gather_launches = eng->graph_stats[1];
+        eng->stat_tiles = eng->graph_stats[2];
     } else {
         TRY(enqueue(eng, d_bytes, d_off, d_thr, flags, true));
     }

@@ -135,6 +135,7 @@ struct cobs_engine {
     // CUDA graph of the batched sequence
     cudaGraphExec_t gexec = nullptr;
     std::vector<uint64_t> gsig;
+    uint64_t graph_stats[3] = {0, 0, 0};  // kernels, gather kernels, tiles in the graph
 
     // timing
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};

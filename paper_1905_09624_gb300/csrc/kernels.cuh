@@ -10,7 +10,7 @@ namespace cobs {
 // Query-term table: shared-memory slots per CTA before the set spills to global memory.
 constexpr uint32_t TERMS_SMEM_SLOTS = 4096;   // 32 KB
 constexpr uint32_t TERMS_THREADS = 256;
-constexpr uint32_t TERMS_SEG = 64;            // positions per rolling segment
+constexpr uint32_t TERMS_SEG = 8;             // windows rolled by one thread per round
 
 struct TermsArgs {
     const uint8_t *bytes;          // queries concatenated

@@ -2,12 +2,25 @@
 // (Sec. 2.1), canonical form (Sec. 2.3), the distinct set G_q(P) via an
 // open-addressing set, then for every distinct term and every block b and hash
 // i < h its row XXH64(term, i) mod w_b (Sec. 2.2), written as a u32 row index.
+//
+// The query is processed in rounds of TERMS_ROUND windows.  Each round stages
+// its bytes in shared memory (coalesced loads), then
+//   phase A: every thread rolls the 2-bit codes of TERMS_SEG consecutive windows
+//            and writes the window codes to shared memory;
+//   phase B: every thread takes one window at a time: hash, set insertion, and
+//            the warp-aggregated append of fresh terms with their row indices.
 #include "kernels.cuh"
 
 namespace cobs {
 
+constexpr uint32_t TERMS_ROUND = TERMS_THREADS * TERMS_SEG;  // windows per round
+constexpr uint32_t TERMS_STAGE_BYTES = TERMS_ROUND + 32;      // + k - 1 <= 31 bytes of overlap
+
 __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     extern __shared__ unsigned long long s_table[];
+    __shared__ __align__(16) uint8_t s_bytes[TERMS_STAGE_BYTES];
+    __shared__ unsigned long long s_code[TERMS_ROUND];
+    __shared__ uint8_t s_valid[TERMS_ROUND];
     __shared__ uint32_t s_ell;
     __shared__ uint32_t s_has_empty;
 
@@ -21,31 +34,41 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
 
     for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) table[i] = EMPTY_KEY;
     if (threadIdx.x == 0) { s_ell = 0; s_has_empty = 0; }
-    __syncthreads();
 
     const uint8_t *src = a.bytes + off0;
     const uint64_t mask = kmer_mask(k);
     const uint64_t base = a.term_base[q];
     const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t nseg = (npos + TERMS_SEG - 1) / TERMS_SEG;
-    // Every thread runs the same number of outer iterations so that the warp-level
-    // append below always sees the full warp.
-    const uint64_t iters = (nseg + blockDim.x - 1) / blockDim.x;
-    for (uint64_t it = 0; it < iters; it++) {
-        uint64_t seg = it * blockDim.x + threadIdx.x;
-        uint64_t p0 = seg * TERMS_SEG;
-        uint64_t p1 = p0 + TERMS_SEG < npos ? p0 + TERMS_SEG : npos;
-        Roller r;
-        roll_init(r);
-        uint64_t ib = p0, ie = p1 > p0 ? p1 + k - 1 : p0;  // bytes feeding windows [p0, p1)
-        // One step per byte; the loop count is the same for all lanes of a full
-        // segment, and lanes past the end simply push nothing.
-        for (uint64_t step = 0; step < TERMS_SEG + 64; step++) {
-            uint64_t i = ib + step;
-            bool in = i < ie;
-            uint64_t code = 0;
-            bool term = false;
-            if (in) term = roll_push(r, src[i], a.kind, k, mask, &code);
+
+    for (uint64_t r0 = 0; r0 < npos; r0 += TERMS_ROUND) {
+        const uint32_t rn = (uint32_t)(npos - r0 < TERMS_ROUND ? npos - r0 : TERMS_ROUND);
+        const uint32_t nbytes = rn + k - 1;
+        __syncthreads();  // previous round finished with s_bytes / s_code (and the table init)
+        for (uint32_t i = threadIdx.x; i < nbytes; i += blockDim.x) s_bytes[i] = src[r0 + i];
+        __syncthreads();
+        // phase A: rolling codes of windows [w0, w1)
+        {
+            const uint32_t w0 = threadIdx.x * TERMS_SEG;
+            const uint32_t w1 = w0 + TERMS_SEG < rn ? w0 + TERMS_SEG : rn;
+            if (w0 < w1) {
+                Roller r;
+                roll_init(r);
+                for (uint32_t i = w0; i < w1 + k - 1; i++) {
+                    uint64_t code = 0;
+                    bool term = roll_push(r, s_bytes[i], a.kind, k, mask, &code);
+                    if (i + 1 >= w0 + k) {  // the window ending at byte i starts at i + 1 - k >= w0
+                        const uint32_t w = i + 1 - k;
+                        s_code[w] = code;
+                        s_valid[w] = term ? 1 : 0;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // phase B: one window per thread and iteration (uniform trip count per warp)
+        for (uint32_t w = threadIdx.x; w < ((rn + 31u) & ~31u); w += blockDim.x) {
+            const bool term = w < rn && s_valid[w];
+            const uint64_t code = term ? s_code[w] : 0;
             bool fresh = false;
             uint64_t h0 = 0;
             if (term) {
@@ -53,25 +76,24 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
                 if (code == EMPTY_KEY) fresh = atomicExch(&s_has_empty, 1u) == 0u;
                 else fresh = set_insert(table, cap, h0, code);
             }
-            // warp-aggregated append of the fresh terms
-            uint32_t m = __ballot_sync(0xffffffffu, fresh);
-            uint32_t slot0 = 0;
+            const uint32_t m = __ballot_sync(0xffffffffu, fresh);
             if (m) {
-                if (lane == (uint32_t)(__ffs(m) - 1)) slot0 = atomicAdd(&s_ell, (uint32_t)__popc(m));
-                slot0 = __shfl_sync(0xffffffffu, slot0, __ffs(m) - 1);
-            }
-            if (fresh) {
-                uint32_t t = slot0 + __popc(m & ((1u << lane) - 1u));
-                for (uint32_t i2 = 0; i2 < a.h; i2++) {
-                    uint64_t hv = i2 == 0 ? h0 : xxh64_u64(code, i2);
-                    for (uint32_t b = 0; b < a.n_blocks; b++) {
-                        DevBlock blk = a.blocks[b];
-                        uint32_t row = barrett_mod(hv, blk.barrett_m, blk.w);
-                        a.rows_idx[(uint64_t)(b * a.h + i2) * a.tcap + base + t] = row;
+                uint32_t slot0 = 0;
+                const uint32_t leader = __ffs(m) - 1;
+                if (lane == leader) slot0 = atomicAdd(&s_ell, (uint32_t)__popc(m));
+                slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+                if (fresh) {
+                    const uint32_t t = slot0 + __popc(m & ((1u << lane) - 1u));
+                    for (uint32_t i2 = 0; i2 < a.h; i2++) {
+                        const uint64_t hv = i2 == 0 ? h0 : xxh64_u64(code, i2);
+                        for (uint32_t b = 0; b < a.n_blocks; b++) {
+                            const DevBlock blk = a.blocks[b];
+                            a.rows_idx[(uint64_t)(b * a.h + i2) * a.tcap + base + t] =
+                                barrett_mod(hv, blk.barrett_m, blk.w);
+                        }
                     }
                 }
             }
-            if (__all_sync(0xffffffffu, !(i + 1 < ie))) break;
         }
     }
     __syncthreads();
@@ -80,7 +102,13 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
 
 void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s) {
     if (n_queries == 0) return;
-    k_query_terms<<<n_queries, TERMS_THREADS, TERMS_SMEM_SLOTS * sizeof(unsigned long long), s>>>(a);
+    static bool attr_set = false;
+    const int dyn = TERMS_SMEM_SLOTS * sizeof(unsigned long long);
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_query_terms, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        attr_set = true;
+    }
+    k_query_terms<<<n_queries, TERMS_THREADS, dyn, s>>>(a);
 }
 
 }  // namespace cobs

@@ -65,6 +65,16 @@ def test_compact_forms(compact, flags):
     assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
 
 
+def test_flat_result_arrays_match_lists(compact):
+    wl, ref, dix = compact
+    eng = cobs.Engine(dix)
+    lists = eng.query_host(wl.queries, wl.q_off, wl.thresholds, cobs.COBS_BATCHED)
+    ell, mn, off, ids, sc = eng.query_host_arrays(wl.queries, wl.q_off, wl.thresholds, cobs.COBS_BATCHED)
+    for i, g in enumerate(lists):
+        assert (ell[i], mn[i]) == (g[0], g[1])
+        assert np.array_equal(ids[off[i]:off[i + 1]], g[2]) and np.array_equal(sc[off[i]:off[i + 1]], g[3])
+
+
 def test_many_hits_large_segments():
     # K = 1 permille: every document with one matching term is a hit, so hit lists
     # exceed the shared-memory sort and use the global merge passes.
