@@ -173,8 +173,13 @@ typedef struct cobs_engine_cfg {
     uint64_t max_queries;
     uint64_t max_query_bytes;
     uint64_t max_hits;        /* initial hit capacity (0 = 1M); grows and re-runs on overflow */
-    uint32_t slice_bytes;     /* batched row-slice width: 32, 64 or 128; 0 = autotune */
-    uint32_t ctas_per_sm;     /* persistent grid = SMs * ctas_per_sm; 0 = autotune */
+    uint32_t slice_bytes;     /* batched row-slice width: 32, 64 or 128; 0 = default (128) */
+    uint32_t ctas_per_sm;     /* persistent grid = SMs * ctas_per_sm; 0 = full occupancy */
+    uint32_t l2_hints;        /* L2 eviction priority of the batched gather's loads:
+                                 0 = default (3), 1 = none, 2 = row indices evict-first,
+                                 3 = row indices evict-first and index rows evict-last,
+                                 4 = index rows evict-last */
+    uint32_t _pad;
 } cobs_engine_cfg;
 
 cobs_status cobs_engine_create(cobs_device_index *dix, const cobs_engine_cfg *cfg, void *stream,
@@ -210,7 +215,7 @@ cobs_status cobs_engine_download(cobs_engine *eng, cobs_result **out);
 typedef struct cobs_query_stats {
     double ms_terms, ms_gather, ms_hits, ms_total;
     uint64_t row_bytes, terms, n_tiles, gather_launches, launches;
-    uint32_t slice_bytes, ctas_per_sm;
+    uint32_t slice_bytes, ctas_per_sm, l2_hints, _pad;
 } cobs_query_stats;
 cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out);
 

@@ -56,14 +56,16 @@ class cobs_result(ctypes.Structure):
 
 class cobs_engine_cfg(ctypes.Structure):
     _fields_ = [("max_queries", ctypes.c_uint64), ("max_query_bytes", ctypes.c_uint64), ("max_hits", ctypes.c_uint64),
-                ("slice_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
+                ("slice_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("l2_hints", ctypes.c_uint32),
+                ("_pad", ctypes.c_uint32)]
 
 
 class cobs_query_stats(ctypes.Structure):
     _fields_ = [("ms_terms", ctypes.c_double), ("ms_gather", ctypes.c_double), ("ms_hits", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("row_bytes", ctypes.c_uint64), ("terms", ctypes.c_uint64),
                 ("n_tiles", ctypes.c_uint64), ("gather_launches", ctypes.c_uint64), ("launches", ctypes.c_uint64),
-                ("slice_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
+                ("slice_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("l2_hints", ctypes.c_uint32),
+                ("_pad", ctypes.c_uint32)]
 
 
 class cobs_serve_cfg(ctypes.Structure):
@@ -310,9 +312,9 @@ class DeviceIndex:
 class Engine:
     """cobs_engine: reusable query workspace on one device index."""
 
-    def __init__(self, dix: DeviceIndex, stream=None, slice_bytes=0, ctas_per_sm=0, max_hits=0):
+    def __init__(self, dix: DeviceIndex, stream=None, slice_bytes=0, ctas_per_sm=0, max_hits=0, l2_hints=0):
         self.dix = dix
-        cfg = cobs_engine_cfg(0, 0, max_hits, slice_bytes, ctas_per_sm)
+        cfg = cobs_engine_cfg(0, 0, max_hits, slice_bytes, ctas_per_sm, l2_hints, 0)
         h = vp()
         check(lib().cobs_engine_create(dix.h, ctypes.byref(cfg), stream, ctypes.byref(h)), "cobs_engine_create")
         self.h = h
@@ -369,7 +371,7 @@ class Engine:
         cfg = cobs_engine_cfg()
         check(lib().cobs_engine_autotune(self.h, _ptr(q_dev), _ptr(off_dev), _ptr(off_host), _ptr(thr_dev),
                                          len(off_host) - 1, ctypes.byref(cfg)), "cobs_engine_autotune")
-        return dict(slice_bytes=cfg.slice_bytes, ctas_per_sm=cfg.ctas_per_sm)
+        return dict(slice_bytes=cfg.slice_bytes, ctas_per_sm=cfg.ctas_per_sm, l2_hints=cfg.l2_hints)
 
 
 class Server:

@@ -230,9 +230,28 @@ constexpr int PIPE_THREADS = PIPE_WARPS * 32;
 constexpr int PIPE_G = 16;
 constexpr int PIPE_D = 3;
 
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, uint32_t src_bytes) {
+// L2 eviction-priority policy: 0 normal, 1 evict first, 2 evict last.
+__device__ __forceinline__ uint64_t l2_policy(uint32_t kind) {
+    uint64_t p;
+    if (kind == 1) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+    else if (kind == 2) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+    else asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, uint32_t src_bytes, uint64_t pol) {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_bytes) : "memory");
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;\n" ::"r"(d), "l"(gsrc),
+                 "r"(src_bytes), "l"(pol)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint4 ldg_hint(const void *p, uint64_t pol) {
+    uint4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;\n"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -288,23 +307,24 @@ __device__ __forceinline__ void hs16_stage(uint32_t (&lv)[4][L], const uint4 *st
     ripple<4, L>(lv, six);
 }
 
-__device__ __forceinline__ void load_idx16(const uint32_t *ridx, uint32_t g, uint32_t ng, uint32_t (&r)[16]) {
+__device__ __forceinline__ void load_idx16(const uint32_t *ridx, uint32_t g, uint32_t ng, uint32_t (&r)[16],
+                                           uint64_t pol) {
     if (g < ng) {
 #pragma unroll
         for (int j = 0; j < 16; j += 4) {
-            uint4 v = __ldg(reinterpret_cast<const uint4 *>(ridx + g * 16u + j));
+            uint4 v = ldg_hint(ridx + g * 16u + j, pol);
             r[j] = v.x; r[j + 1] = v.y; r[j + 2] = v.z; r[j + 3] = v.w;
         }
     }
 }
 
 __device__ __forceinline__ void issue16(uint4 *stage_lane, const uint8_t *colbase, uint32_t rowbytes,
-                                        const uint32_t (&r)[16], uint32_t t0, uint32_t n) {
+                                        const uint32_t (&r)[16], uint32_t t0, uint32_t n, uint64_t pol) {
 #pragma unroll
     for (int j = 0; j < 16; j++) {
         const bool ok = t0 + j < n;
         const uint8_t *src = ok ? colbase + (uint64_t)r[j] * rowbytes : colbase;
-        cp_async16(stage_lane + j * 32, src, ok ? 16u : 0u);
+        cp_async16(stage_lane + j * 32, src, ok ? 16u : 0u, pol);
     }
 }
 
@@ -317,6 +337,8 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_gather_pipe(GatherArgs a) {
     const uint32_t qslot = lane / LPQ;
     const uint32_t c = lane % LPQ;
     const unsigned long long n_tiles = (unsigned long long)a.n_slices * a.n_groups;
+    const uint64_t pol_idx = l2_policy(a.l2_idx_policy);
+    const uint64_t pol_row = l2_policy(a.l2_row_policy);
     for (;;) {
         unsigned long long tile = 0;
         if (lane == 0) tile = atomicAdd(a.work_counter, 1ULL);
@@ -344,28 +366,28 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_gather_pipe(GatherArgs a) {
 #pragma unroll
             for (int l = 0; l < L; l++) lv[w][l] = 0u;
         uint32_t ra[16], rb[16];
-        load_idx16(ridx, 0, ng, ra);
-        load_idx16(ridx, 1, ng, rb);
+        load_idx16(ridx, 0, ng, ra, pol_idx);
+        load_idx16(ridx, 1, ng, rb, pol_idx);
         uint32_t gi = 0, si = 0;  // next group to issue, its stage
 #pragma unroll
         for (int p = 0; p < PIPE_D - 1; p++) {
-            if (gi < ng) issue16(&s_stage[warp][si][0][lane], colbase, rowbytes, ra, gi * 16u, n);
+            if (gi < ng) issue16(&s_stage[warp][si][0][lane], colbase, rowbytes, ra, gi * 16u, n, pol_row);
             cp_async_commit();
             gi++;
             si = si + 1 == PIPE_D ? 0 : si + 1;
 #pragma unroll
             for (int j = 0; j < 16; j++) ra[j] = rb[j];
-            load_idx16(ridx, gi + 1, ng, rb);
+            load_idx16(ridx, gi + 1, ng, rb, pol_idx);
         }
         uint32_t sc = 0;  // stage being consumed
         for (uint32_t g = 0; g < ng; g++) {
-            if (gi < ng) issue16(&s_stage[warp][si][0][lane], colbase, rowbytes, ra, gi * 16u, n);
+            if (gi < ng) issue16(&s_stage[warp][si][0][lane], colbase, rowbytes, ra, gi * 16u, n, pol_row);
             cp_async_commit();
             gi++;
             si = si + 1 == PIPE_D ? 0 : si + 1;
 #pragma unroll
             for (int j = 0; j < 16; j++) ra[j] = rb[j];
-            load_idx16(ridx, gi + 1, ng, rb);
+            load_idx16(ridx, gi + 1, ng, rb, pol_idx);
             cp_async_wait<PIPE_D - 1>();
             hs16_stage<L>(lv, &s_stage[warp][sc][0][lane]);
             sc = sc + 1 == PIPE_D ? 0 : sc + 1;

@@ -513,6 +513,11 @@ extern "C" cobs_status cobs_engine_create(cobs_device_index *dix, const cobs_eng
     eng->lanes_per_query = sb / 16;
     int occ = gather_batched_max_blocks_per_sm(eng->lanes_per_query, dix->params.num_hashes);
     eng->ctas_per_sm = eng->cfg.ctas_per_sm ? eng->cfg.ctas_per_sm : (uint32_t)std::max(occ, 1);
+    if (eng->cfg.l2_hints > 4) {
+        cobs_engine_free(eng);
+        return set_error(COBS_ERR_ARG, "l2_hints must be 0..4");
+    }
+    eng->l2_hints = eng->cfg.l2_hints ? eng->cfg.l2_hints : 3;
     eng->hit_cap = eng->cfg.max_hits ? eng->cfg.max_hits : (1ULL << 20);
     for (auto &e : eng->ev) cudaEventCreate(&e);
     cudaEventCreateWithFlags(&eng->ev_done, cudaEventDisableTiming);
@@ -597,6 +602,7 @@ static cobs_status ensure_buffers(cobs_engine *eng, const BatchPlan &bp) {
     CU(eng->qcursor.ensure(n * 4));
     CU(eng->hitoff.ensure((n + 1) * 8));
     CU(eng->rows_idx.ensure(std::max<uint64_t>(nb, 1) * h * bp.tcap * 4));
+    CU(eng->codes.ensure(bp.tcap * 8));
     CU(eng->tables.ensure(bp.total_slots * 8));
     CU(eng->raw_q.ensure(eng->hit_cap * 4));
     CU(eng->raw_key.ensure(eng->hit_cap * 8));
@@ -646,6 +652,7 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
     ta.tables = eng->tables.as<unsigned long long>();
     ta.ell = eng->ell.as<uint32_t>();
     ta.rows_idx = eng->rows_idx.as<uint32_t>();
+    ta.codes = eng->codes.as<unsigned long long>();
     ta.tcap = bp.tcap;
     ta.blocks = dix->dblocks.as<DevBlock>();
     ta.n_blocks = (uint32_t)dix->blocks.size();
@@ -724,6 +731,9 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
             ga.raw_q = eng->raw_q.as<uint32_t>();
             ga.raw_key = eng->raw_key.as<unsigned long long>();
             ga.hit_cap = eng->hit_cap;
+            // l2_hints: 1 none, 2 row indices evict-first, 3 + index rows evict-last, 4 rows evict-last only
+            ga.l2_idx_policy = (eng->l2_hints == 2 || eng->l2_hints == 3) ? 1u : 0u;
+            ga.l2_row_policy = (eng->l2_hints == 3 || eng->l2_hints == 4) ? 2u : 0u;
             if (ga.n_slices == 0 || ga.n_groups == 0) continue;
             launch_gather_batched_L(ga, eng->lanes_per_query, cl.L, grid, s);
             eng->stat_launches += 1;
@@ -769,8 +779,9 @@ static std::vector<uint64_t> graph_signature(cobs_engine *eng, const uint8_t *d_
                                              const uint16_t *d_thr) {
     const BatchPlan &bp = eng->bp;
     std::vector<uint64_t> sig = {bp.n, bp.tcap, bp.total_slots, (uint64_t)d_bytes, (uint64_t)d_off, (uint64_t)d_thr,
-                                 eng->hit_cap, eng->lanes_per_query, eng->ctas_per_sm,
+                                 eng->hit_cap, eng->lanes_per_query, eng->ctas_per_sm, eng->l2_hints,
                                  (uint64_t)eng->rows_idx.p, (uint64_t)eng->tables.p, (uint64_t)eng->raw_q.p,
+                                 (uint64_t)eng->codes.p,
                                  (uint64_t)eng->plan.p, (uint64_t)eng->pin_plan.p, (uint64_t)eng->qcount.p,
                                  (uint64_t)eng->ell.p, (uint64_t)eng->minsc.p, (uint64_t)eng->qcursor.p,
                                  (uint64_t)eng->hitoff.p, (uint64_t)eng->raw_key.p, (uint64_t)eng->keys.p,
@@ -963,13 +974,18 @@ extern "C" cobs_status cobs_engine_query_host(cobs_engine *eng, const uint8_t *q
     CU(eng->qbytes.ensure(total));
     CU(eng->qoff.ensure((n + 1) * 8));
     CU(eng->thr.ensure(n * 2 + 16));
+    // Query bytes in page-locked memory are copied by DMA straight from the
+    // caller's buffer; pageable bytes go through the engine's pinned staging.
+    cudaPointerAttributes pa{};
+    const bool pinned = total && cudaPointerGetAttributes(&pa, queries) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+    cudaGetLastError();  // clear a lookup failure on pageable memory
     uint8_t *pin = eng->pin_in.as<uint8_t>();
-    if (total) memcpy(pin, queries, total);
+    if (total && !pinned) memcpy(pin, queries, total);
     uint64_t o1 = (total + 15) / 16 * 16, o2 = o1 + (n + 1) * 8;
     memcpy(pin + o1, offsets, (n + 1) * 8);
     if (n) memcpy(pin + o2, thr, n * 2);
     cudaStream_t s = eng->stream;
-    if (total) CU(cudaMemcpyAsync(eng->qbytes.p, pin, total, cudaMemcpyHostToDevice, s));
+    if (total) CU(cudaMemcpyAsync(eng->qbytes.p, pinned ? queries : pin, total, cudaMemcpyHostToDevice, s));
     CU(cudaMemcpyAsync(eng->qoff.p, pin + o1, (n + 1) * 8, cudaMemcpyHostToDevice, s));
     if (n) CU(cudaMemcpyAsync(eng->thr.p, pin + o2, n * 2, cudaMemcpyHostToDevice, s));
     TRY(engine_query(eng, eng->qbytes.as<uint8_t>(), eng->qoff.as<uint64_t>(), offsets, eng->thr.as<uint16_t>(), n,
@@ -1019,6 +1035,7 @@ extern "C" cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out
     out->launches = eng->stat_launches;
     out->slice_bytes = eng->lanes_per_query * 16;
     out->ctas_per_sm = eng->ctas_per_sm;
+    out->l2_hints = eng->l2_hints;
     return COBS_OK;
 }
 
@@ -1026,34 +1043,48 @@ extern "C" cobs_status cobs_engine_autotune(cobs_engine *eng, const uint8_t *que
                                             const uint64_t *offsets_host, const uint16_t *thr_dev, uint64_t n,
                                             cobs_engine_cfg *cfg_out) {
     if (!eng) return set_error(COBS_ERR_ARG, "NULL engine");
+    // Sweep slice width x resident CTAs per SM x L2 hints; time the gather phase
+    // (CUDA events around the gather kernels), best of the repeats after the first.
     const uint32_t lpqs[3] = {2, 4, 8};
     double best = 1e30;
-    uint32_t best_lpq = eng->lanes_per_query, best_cta = eng->ctas_per_sm;
+    uint32_t best_lpq = eng->lanes_per_query, best_cta = eng->ctas_per_sm, best_hint = eng->l2_hints;
     const int occ_max = std::max(1, gather_batched_max_blocks_per_sm(8, eng->dix->params.num_hashes));
+    std::vector<int> ctas = {occ_max};
+    if (occ_max > 1) ctas.push_back(occ_max / 2);
+    if (occ_max > 2) ctas.push_back(1);
+    const uint32_t hints_h1[4] = {1, 2, 3, 4};
+    const int n_hints = eng->dix->params.num_hashes == 1 ? 4 : 1;  // the h > 1 kernel takes no hints
     for (uint32_t lpq : lpqs) {
         TRY(ensure_slices(eng, lpq));
         eng->lanes_per_query = lpq;
-        for (int cta = 1; cta <= occ_max; cta *= 2) {
+        for (int cta : ctas) {
             eng->ctas_per_sm = (uint32_t)cta;
-            double tot = 0;
-            for (int rep = 0; rep < 3; rep++) {
-                TRY(engine_query(eng, queries_dev, offsets_dev, offsets_host, thr_dev, n, COBS_BATCHED));
-                TRY(engine_finish(eng));
-                float t = 0;
-                cudaEventElapsedTime(&t, eng->ev[1], eng->ev[2]);
-                if (rep) tot += t;
+            for (int hi = 0; hi < n_hints; hi++) {
+                eng->l2_hints = n_hints == 1 ? eng->l2_hints : hints_h1[hi];
+                double tbest = 1e30;
+                for (int rep = 0; rep < 3; rep++) {
+                    TRY(engine_query(eng, queries_dev, offsets_dev, offsets_host, thr_dev, n, COBS_BATCHED));
+                    TRY(engine_finish(eng));
+                    float t = 0;
+                    cudaEventElapsedTime(&t, eng->ev[1], eng->ev[2]);
+                    if (rep) tbest = std::min(tbest, (double)t);
+                }
+                if (getenv("COBS_AUTOTUNE_VERBOSE"))
+                    fprintf(stderr, "autotune slice=%u ctas=%d l2_hints=%u gather_ms=%.4f\n", lpq * 16, cta,
+                            eng->l2_hints, tbest);
+                if (tbest < best) {
+                    best = tbest;
+                    best_lpq = lpq;
+                    best_cta = (uint32_t)cta;
+                    best_hint = eng->l2_hints;
+                }
             }
-            if (tot < best) {
-                best = tot;
-                best_lpq = lpq;
-                best_cta = (uint32_t)cta;
-            }
-            if (cta < occ_max && cta * 2 > occ_max) cta = occ_max / 2;  // also try the full occupancy
         }
     }
     TRY(ensure_slices(eng, best_lpq));
     eng->lanes_per_query = best_lpq;
     eng->ctas_per_sm = best_cta;
+    eng->l2_hints = best_hint;
     if (eng->gexec) {
         cudaGraphExecDestroy(eng->gexec);
         eng->gexec = nullptr;
@@ -1062,6 +1093,7 @@ extern "C" cobs_status cobs_engine_autotune(cobs_engine *eng, const uint8_t *que
         *cfg_out = eng->cfg;
         cfg_out->slice_bytes = best_lpq * 16;
         cfg_out->ctas_per_sm = best_cta;
+        cfg_out->l2_hints = best_hint;
     }
     return COBS_OK;
 }

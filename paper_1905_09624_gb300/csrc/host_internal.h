@@ -108,6 +108,7 @@ struct cobs_engine {
     cobs_engine_cfg cfg{};
     int n_sm = 0;
     uint32_t lanes_per_query = 8;
+    uint32_t l2_hints = 3;
     uint32_t ctas_per_sm = 1;
     uint64_t hit_cap = 0;
 
@@ -116,7 +117,7 @@ struct cobs_engine {
     cobs::DevBuf plan;                        // term_base | table_base | order
     cobs::DevBuf ell, minsc, qcount, qcursor, hitoff;
     cobs::DevBuf counters;                    // [0] hit count, [1..] work counters
-    cobs::DevBuf rows_idx, tables;
+    cobs::DevBuf rows_idx, tables, codes;
     cobs::DevBuf raw_q, raw_key, keys, tmp, out_ids, out_scores;
     cobs::DevBuf scores;                      // plain form, per sorted position
     cobs::DevBuf slices;

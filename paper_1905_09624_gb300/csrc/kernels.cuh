@@ -11,6 +11,8 @@ namespace cobs {
 constexpr uint32_t TERMS_SMEM_SLOTS = 4096;   // 32 KB
 constexpr uint32_t TERMS_THREADS = 256;
 constexpr uint32_t TERMS_SEG = 8;             // windows rolled by one thread per round
+constexpr uint32_t TERMS_BUCKET_BITS = 6;     // terms are emitted in 64 row buckets per block
+constexpr uint32_t TERMS_BUCKETS = 1u << TERMS_BUCKET_BITS;
 
 struct TermsArgs {
     const uint8_t *bytes;          // queries concatenated
@@ -20,6 +22,7 @@ struct TermsArgs {
     unsigned long long *tables;    // global sets
     uint32_t *ell;                 // out: distinct terms per query
     uint32_t *rows_idx;            // out: row of term t for (block b, hash i) at [(b*h+i)*tcap + base + t]
+    unsigned long long *codes;     // scratch: distinct term codes, tcap entries
     uint64_t tcap;
     const DevBlock *blocks;
     uint32_t n_blocks, h, kind, k;
@@ -53,6 +56,8 @@ struct GatherArgs {
     uint32_t *raw_q;               // raw hits: query
     unsigned long long *raw_key;   // raw hits: (~score << 32) | original id
     uint64_t hit_cap;
+    uint32_t l2_idx_policy;        // L2 eviction priority of row-index loads: 0 normal, 1 first, 2 last
+    uint32_t l2_row_policy;        // same for the gathered index rows
 };
 // lanes_per_query in {2, 4, 8}: slice = 16 * lanes_per_query bytes.  L = counter
 // levels (8, 12, 16 or 24): every query of the launch has fewer than 2^L terms.

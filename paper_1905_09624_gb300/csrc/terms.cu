@@ -82,22 +82,57 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
                 const uint32_t leader = __ffs(m) - 1;
                 if (lane == leader) slot0 = atomicAdd(&s_ell, (uint32_t)__popc(m));
                 slot0 = __shfl_sync(0xffffffffu, slot0, leader);
-                if (fresh) {
-                    const uint32_t t = slot0 + __popc(m & ((1u << lane) - 1u));
-                    for (uint32_t i2 = 0; i2 < a.h; i2++) {
-                        const uint64_t hv = i2 == 0 ? h0 : xxh64_u64(code, i2);
-                        for (uint32_t b = 0; b < a.n_blocks; b++) {
-                            const DevBlock blk = a.blocks[b];
-                            a.rows_idx[(uint64_t)(b * a.h + i2) * a.tcap + base + t] =
-                                barrett_mod(hv, blk.barrett_m, blk.w);
-                        }
-                    }
-                }
+                if (fresh) a.codes[base + slot0 + __popc(m & ((1u << lane) - 1u))] = code;
             }
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) a.ell[q] = s_ell;
+    const uint32_t ell = s_ell;
+    if (threadIdx.x == 0) a.ell[q] = ell;
+
+    // phase C: per block, the distinct terms' rows in row-bucket order (a counting
+    // sort by the top bits of the hash-0 row).  Scores do not depend on the order
+    // of the terms; bucketed order makes all warps of the gather sweep the rows of
+    // a slice together, so the rows in use at any moment form a narrow band.
+    __shared__ uint32_t s_hist[TERMS_BUCKETS];
+    for (uint32_t b = 0; b < a.n_blocks; b++) {
+        const DevBlock blk = a.blocks[b];
+        const int lg = 32 - __clz(blk.w > 1 ? blk.w - 1 : 0);   // bits of the largest row
+        const uint32_t shift = lg > TERMS_BUCKET_BITS ? (uint32_t)(lg - TERMS_BUCKET_BITS) : 0u;
+        for (uint32_t i = threadIdx.x; i < TERMS_BUCKETS; i += blockDim.x) s_hist[i] = 0;
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < ell; t += blockDim.x) {
+            const uint32_t r0 = barrett_mod(xxh64_u64(a.codes[base + t], 0), blk.barrett_m, blk.w);
+            atomicAdd(&s_hist[r0 >> shift], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {  // exclusive scan of the bucket counts by one warp
+            uint32_t carry = 0;
+            for (uint32_t c0 = 0; c0 < TERMS_BUCKETS; c0 += 32) {
+                const uint32_t v = s_hist[c0 + lane];
+                uint32_t x = v;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+                    if ((int)lane >= d) x += y;
+                }
+                s_hist[c0 + lane] = carry + x - v;
+                carry += __shfl_sync(0xffffffffu, x, 31);
+            }
+        }
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < ell; t += blockDim.x) {
+            const uint64_t code = a.codes[base + t];
+            const uint64_t h0 = xxh64_u64(code, 0);
+            const uint32_t r0 = barrett_mod(h0, blk.barrett_m, blk.w);
+            const uint32_t pos = atomicAdd(&s_hist[r0 >> shift], 1u);
+            a.rows_idx[(uint64_t)(b * a.h) * a.tcap + base + pos] = r0;
+            for (uint32_t i2 = 1; i2 < a.h; i2++)
+                a.rows_idx[(uint64_t)(b * a.h + i2) * a.tcap + base + pos] =
+                    barrett_mod(xxh64_u64(code, i2), blk.barrett_m, blk.w);
+        }
+        __syncthreads();
+    }
 }
 
 void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s) {
