@@ -286,9 +286,10 @@ __device__ __forceinline__ void ripple(uint32_t (&lv)[4][L], W4 c) {
             c.v[w] = t;
         }
 }
-// Harley-Seal tree over the 16 rows of one stage (stride 32 uint4 = one per lane).
+// Harley-Seal tree over the 16 rows of one stage (stride 32 uint4 = one per lane);
+// returns the carry of weight 16 (added to level 4 by the caller).
 template <int L>
-__device__ __forceinline__ void hs16_stage(uint32_t (&lv)[4][L], const uint4 *st) {
+__device__ __forceinline__ W4 hs16_stage(uint32_t (&lv)[4][L], const uint4 *st) {
     W4 tA = csa_lv<0>(lv, w4(st[0 * 32]), w4(st[1 * 32]));
     W4 tB = csa_lv<0>(lv, w4(st[2 * 32]), w4(st[3 * 32]));
     W4 fA = csa_lv<1>(lv, tA, tB);
@@ -303,8 +304,7 @@ __device__ __forceinline__ void hs16_stage(uint32_t (&lv)[4][L], const uint4 *st
     tB = csa_lv<0>(lv, w4(st[14 * 32]), w4(st[15 * 32]));
     fB = csa_lv<1>(lv, tA, tB);
     W4 eB = csa_lv<2>(lv, fA, fB);
-    W4 six = csa_lv<3>(lv, eA, eB);
-    ripple<4, L>(lv, six);
+    return csa_lv<3>(lv, eA, eB);
 }
 
 __device__ __forceinline__ void load_idx16(const uint32_t *ridx, uint32_t g, uint32_t ng, uint32_t (&r)[16],
@@ -380,6 +380,10 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_gather_pipe(GatherArgs a) {
             load_idx16(ridx, gi + 1, ng, rb, pol_idx);
         }
         uint32_t sc = 0;  // stage being consumed
+        // carries of weight 16 are paired by one more full adder at level 4, so
+        // only every second group ripples (from level 5) into the upper levels
+        W4 pend;
+        bool has_pend = false;
         for (uint32_t g = 0; g < ng; g++) {
             if (gi < ng) issue16(&s_stage[warp][si][0][lane], colbase, rowbytes, ra, gi * 16u, n, pol_row);
             cp_async_commit();
@@ -389,9 +393,16 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_gather_pipe(GatherArgs a) {
             for (int j = 0; j < 16; j++) ra[j] = rb[j];
             load_idx16(ridx, gi + 1, ng, rb, pol_idx);
             cp_async_wait<PIPE_D - 1>();
-            hs16_stage<L>(lv, &s_stage[warp][sc][0][lane]);
+            const W4 six = hs16_stage<L>(lv, &s_stage[warp][sc][0][lane]);
+            if (has_pend) {
+                ripple<5, L>(lv, csa_lv<4>(lv, pend, six));
+            } else {
+                pend = six;
+            }
+            has_pend = !has_pend;
             sc = sc + 1 == PIPE_D ? 0 : sc + 1;
         }
+        if (has_pend) ripple<4, L>(lv, pend);
         cp_async_wait<0>();
         if (n) emit_hits<L>(a, blk, col, q, ell, lv);
     }

@@ -30,7 +30,8 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     const uint32_t k = a.k;
     const uint64_t npos = len >= k ? len - k + 1 : 0;
     const uint32_t cap = (uint32_t)set_slots(npos);
-    unsigned long long *table = cap <= TERMS_SMEM_SLOTS ? s_table : a.tables + a.table_base[q];
+    const bool in_smem = cap <= TERMS_SMEM_SLOTS;
+    unsigned long long *table = in_smem ? s_table : a.tables + a.table_base[q];
 
     for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) table[i] = EMPTY_KEY;
     if (threadIdx.x == 0) { s_ell = 0; s_has_empty = 0; }
@@ -82,13 +83,48 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
                 const uint32_t leader = __ffs(m) - 1;
                 if (lane == leader) slot0 = atomicAdd(&s_ell, (uint32_t)__popc(m));
                 slot0 = __shfl_sync(0xffffffffu, slot0, leader);
-                if (fresh) a.codes[base + slot0 + __popc(m & ((1u << lane) - 1u))] = code;
+                // a set in shared memory is compacted after the rounds; a spilled set
+                // keeps a compact list instead (the hash-0 value when h == 1, which is
+                // all phase C needs, else the code)
+                if (fresh && !in_smem)
+                    a.codes[base + slot0 + __popc(m & ((1u << lane) - 1u))] = a.h == 1 ? h0 : code;
             }
         }
     }
     __syncthreads();
     const uint32_t ell = s_ell;
     if (threadIdx.x == 0) a.ell[q] = ell;
+    // A set in shared memory holds at most TERMS_ROUND codes (one round): compact
+    // it into the window-code buffer, which is free now.
+    if (in_smem) {
+        __shared__ uint32_t s_fill;
+        if (threadIdx.x == 0) s_fill = 0;
+        __syncthreads();
+        for (uint32_t i0 = 0; i0 < cap; i0 += blockDim.x) {
+            const uint32_t i = i0 + threadIdx.x;
+            const uint64_t c = i < cap ? table[i] : EMPTY_KEY;
+            const bool occ = c != EMPTY_KEY;
+            const uint32_t m = __ballot_sync(0xffffffffu, occ);
+            uint32_t p0 = 0;
+            if (m) {
+                const uint32_t leader = __ffs(m) - 1;
+                if (lane == leader) p0 = atomicAdd(&s_fill, (uint32_t)__popc(m));
+                p0 = __shfl_sync(0xffffffffu, p0, leader);
+            }
+            if (occ) s_code[p0 + __popc(m & ((1u << lane) - 1u))] = a.h == 1 ? xxh64_u64(c, 0) : c;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && s_has_empty) s_code[s_fill] = a.h == 1 ? xxh64_u64(EMPTY_KEY, 0) : EMPTY_KEY;
+        __syncthreads();
+    }
+    // every distinct term once, spread over the threads: f(code, hash 0); the code
+    // is only meaningful (and only used) when h > 1
+    auto each_distinct = [&](auto &&f) {
+        for (uint32_t t = threadIdx.x; t < ell; t += blockDim.x) {
+            const uint64_t key = in_smem ? (uint64_t)s_code[t] : (uint64_t)a.codes[base + t];
+            f(key, a.h == 1 ? key : xxh64_u64(key, 0));
+        }
+    };
 
     // phase C: per block, the distinct terms' rows in row-bucket order (a counting
     // sort by the top bits of the hash-0 row).  Scores do not depend on the order
@@ -101,10 +137,10 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
         const uint32_t shift = lg > TERMS_BUCKET_BITS ? (uint32_t)(lg - TERMS_BUCKET_BITS) : 0u;
         for (uint32_t i = threadIdx.x; i < TERMS_BUCKETS; i += blockDim.x) s_hist[i] = 0;
         __syncthreads();
-        for (uint32_t t = threadIdx.x; t < ell; t += blockDim.x) {
-            const uint32_t r0 = barrett_mod(xxh64_u64(a.codes[base + t], 0), blk.barrett_m, blk.w);
+        each_distinct([&](uint64_t, uint64_t h0) {
+            const uint32_t r0 = barrett_mod(h0, blk.barrett_m, blk.w);
             atomicAdd(&s_hist[r0 >> shift], 1u);
-        }
+        });
         __syncthreads();
         if (threadIdx.x < 32) {  // exclusive scan of the bucket counts by one warp
             uint32_t carry = 0;
@@ -121,16 +157,14 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
             }
         }
         __syncthreads();
-        for (uint32_t t = threadIdx.x; t < ell; t += blockDim.x) {
-            const uint64_t code = a.codes[base + t];
-            const uint64_t h0 = xxh64_u64(code, 0);
+        each_distinct([&](uint64_t code, uint64_t h0) {
             const uint32_t r0 = barrett_mod(h0, blk.barrett_m, blk.w);
             const uint32_t pos = atomicAdd(&s_hist[r0 >> shift], 1u);
             a.rows_idx[(uint64_t)(b * a.h) * a.tcap + base + pos] = r0;
             for (uint32_t i2 = 1; i2 < a.h; i2++)
                 a.rows_idx[(uint64_t)(b * a.h + i2) * a.tcap + base + pos] =
                     barrett_mod(xxh64_u64(code, i2), blk.barrett_m, blk.w);
-        }
+        });
         __syncthreads();
     }
 }
