@@ -252,6 +252,43 @@ cobs_status cobs_serve_poll(cobs_server *srv, uint64_t ticket, cobs_hits *out);
 void cobs_hits_release(cobs_server *srv, uint64_t ticket);
 cobs_status cobs_serve_stop(cobs_server *srv, cobs_serve_stats *out);
 
+/* ------------------------------------------------------ no allocation */
+
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory.  Examples: a process whose memory pool (such as
+ * a framework's caching allocator) already holds all the device memory it may
+ * use, and latency-critical request threads that must not call cudaMalloc or
+ * cudaFree, which can synchronise the whole device and stall other streams.
+ *
+ * cobs_query_one_noalloc runs ONE query through the plain kernels (terms,
+ * gather/AND/ADD, threshold, sorted hits) and allocates nothing: no cudaMalloc,
+ * no cudaFree, no allocating library routine.  Its scratch is a fixed array in
+ * the library's device code, about 6.4 MiB, which every GPU that loads the
+ * library holds until the process exits.  Limits: at most
+ * COBS_NOALLOC_MAX_WINDOWS windows in the query, COBS_NOALLOC_MAX_DOCS documents
+ * in the index and COBS_NOALLOC_MAX_ROW_LISTS (blocks x hashes); beyond them the
+ * call returns COBS_ERR_ARG with a message.
+ *
+ * Arguments: query_dev / len: the query bytes (device); thr_permille: K in
+ * 1..1000; out_meta_dev: 3 device uint32 receiving (n_terms, min_score, n_hits);
+ * out_ids_dev / out_scores_dev: device arrays of out_capacity >= n_docs entries
+ * receiving the hits sorted by score descending, then id ascending.  The current
+ * device must be the index's device.  Asynchronous on `stream`: the outputs are
+ * complete when the stream reaches this point.
+ *
+ * The first call on a device looks up the scratch array's device address (once
+ * per device); make that first call before any stream capture.  Every call
+ * shares the one scratch array and leaves its contents behind (each call clears
+ * what must start at zero), so calls that overlap on the GPU -- on different
+ * streams, or from different threads -- race with each other and give wrong
+ * results: serialise them. */
+#define COBS_NOALLOC_MAX_WINDOWS 16384u
+#define COBS_NOALLOC_MAX_DOCS 131072u
+#define COBS_NOALLOC_MAX_ROW_LISTS 32u
+cobs_status cobs_query_one_noalloc(cobs_device_index *dix, const uint8_t *query_dev, uint64_t len,
+                                   uint16_t thr_permille, uint32_t *out_meta_dev, uint32_t *out_ids_dev,
+                                   uint32_t *out_scores_dev, uint64_t out_capacity, void *stream);
+
 /* --------------------------------------------------------------- misc */
 
 const char *cobs_last_error(void);

@@ -116,6 +116,8 @@ _PROTOS = {
     "cobs_serve_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(cobs_hits)]),
     "cobs_hits_release": (None, [vp, ctypes.c_uint64]),
     "cobs_serve_stop": (ctypes.c_int, [vp, ctypes.POINTER(cobs_serve_stats)]),
+    "cobs_query_one_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_uint64, ctypes.c_uint16, vp, vp, vp,
+                                              ctypes.c_uint64, vp]),
     "cobs_last_error": (ctypes.c_char_p, []),
     "cobs_bloom_width": (ctypes.c_uint64, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double]),
     "cobs_version": (ctypes.c_char_p, []),
