@@ -209,6 +209,77 @@ def run_reference(args):
     return 0
 
 
+# -------------------------------------------------------------------- serve
+def run_serve(dix, wl, rates, seconds, verify_oracle=None):
+    """Poisson arrivals (cfg5 recipe on the given index) submitted at their
+    arrival times from one thread, results polled from another; p50/p99 are the
+    library's submit-to-visible latencies.  Optionally checks a seeded 1% sample
+    of the results against the oracle index."""
+    import synth
+    from paper_1905_09624_gb300 import cobs
+    out = []
+    for rate in rates:
+        n = max(50, int(rate * seconds))
+        qb, qo, thr, src, t_arr = synth.config5_queries(wl, n_q=n, rate=rate)
+        ql = [bytes(qb[int(qo[i]):int(qo[i + 1])]) for i in range(n)]
+        srv = cobs.Server(dix, max_inflight_waves=3, max_wave_queries=4096)
+        tickets = [None] * n
+        results = [None] * n
+        done_evt = threading.Event()
+
+        def poller():
+            pending = 0
+            while True:
+                progressed = False
+                for i in range(pending, n):
+                    if tickets[i] is None:
+                        break
+                    if results[i] is None:
+                        r = srv.poll(tickets[i])
+                        if r is None:
+                            break
+                        results[i] = r
+                        progressed = True
+                    if i == pending:
+                        pending += 1
+                if pending >= n:
+                    done_evt.set()
+                    return
+                if not progressed:
+                    time.sleep(0.0002)
+
+        th = threading.Thread(target=poller, daemon=True)
+        th.start()
+        t0 = time.perf_counter()
+        for i in range(n):
+            while time.perf_counter() - t0 < t_arr[i]:
+                pass
+            tickets[i] = srv.submit(ql[i], int(thr[i]))
+        done_evt.wait(timeout=120)
+        stats = srv.stop()
+        terms = sum(int(r[0]) for r in results if r is not None)
+        rec = {"rate_qps": rate, "queries": n, "completed": int(stats["completed"]), "waves": int(stats["waves"]),
+               "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "qps": stats["qps"],
+               "kmers_per_s": terms / stats["seconds"] if stats["seconds"] else None}
+        if verify_oracle is not None:
+            # a seeded 1% sample of the requests, each an independent single-threaded
+            # oracle query (run side by side on the host cores)
+            from concurrent.futures import ThreadPoolExecutor
+            sample = np.random.default_rng(5000 + int(rate)).choice(n, max(1, n // 100), replace=False)
+
+            def same(i):
+                ell, mn, ids, sc = verify_oracle.query(ql[i], int(thr[i]))
+                r = results[i]
+                return int(r is not None and r[0] == ell and r[1] == mn and np.array_equal(r[2], ids)
+                           and np.array_equal(r[3], sc))
+
+            with ThreadPoolExecutor(os.cpu_count() or 4) as ex:
+                ok = sum(ex.map(same, sample.tolist()))
+            rec["oracle_sample"] = f"{ok}/{len(sample)} identical"
+        out.append(rec)
+    return out
+
+
 # ---------------------------------------------------------------------- GPU
 def run_gpu(args):
     import torch
@@ -385,11 +456,16 @@ def run_gpu(args):
     if plain:
         out["plain"]["frac_of_hbm_peak"] = plain["row_gbs_logical"] / peak
 
+    oracle_ix = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         rng = np.random.default_rng(777)
         sample = rng.permutation(wl.n_queries)[:args.cpu_queries].tolist()
-        _, cpu = oracle_baseline(wl, sample, budget_s=args.cpu_budget_s)
+        oracle_ix, cpu = oracle_baseline(wl, sample, budget_s=args.cpu_budget_s)
         out["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if args.serve_rates and args.config == "cfg2":
+        del eng
+        rates = [float(r) for r in args.serve_rates.split(",") if r]
+        out["serve"] = run_serve(dix, wl, rates, args.serve_seconds, verify_oracle=oracle_ix)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
@@ -414,6 +490,9 @@ def main():
     ap.add_argument("--cpu-queries", type=int, default=400)
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--ref-queries-per-step", type=int, default=40)
+    ap.add_argument("--serve-rates", default="1000,10000,50000",
+                    help="Poisson arrival rates (queries/s) of the serving run on the cfg2 index; '' to skip")
+    ap.add_argument("--serve-seconds", type=float, default=1.5)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
