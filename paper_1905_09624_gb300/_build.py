@@ -50,6 +50,8 @@ def build(verbose: bool = False, ptxas_verbose: bool = False, extra_flags=()) ->
     nvcc = _nvcc()
     flags = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
              "-I", INCLUDE, "-I", CSRC] + ARCH + list(extra_flags)
+    # compile-time kernel geometry for experiments, e.g. "-DCOBS_PIPE_G=16 -DCOBS_PIPE_D=3"
+    flags += os.environ.get("COBS_EXTRA_NVCC_FLAGS", "").split()
     if ptxas_verbose:
         flags += ["-Xptxas", "-v"]
     srcs = _sources()

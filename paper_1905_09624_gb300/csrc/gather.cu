@@ -224,11 +224,33 @@ __global__ void __launch_bounds__(GATHER_THREADS) k_gather_batched(GatherArgs a)
 // through a ring of PIPE_D stages of PIPE_G rows in shared memory (cp.async,
 // 16 bytes per lane and row, L2 only), so up to PIPE_D - 1 groups of loads are
 // in flight while the adder tree consumes the oldest group.  Row indices are
-// prefetched two groups ahead in registers.
-constexpr int PIPE_WARPS = 2;
+// prefetched in registers.  The default geometry (16 rows x 2 stages, 2 warps
+// per CTA, 6 CTAs per SM) was the fastest of the measured variants: more
+// resident warps beat deeper rings per warp (the profile record in profiles/
+// lists the sweep).
+#ifndef COBS_PIPE_G
+#define COBS_PIPE_G 16
+#endif
+#ifndef COBS_PIPE_D
+#define COBS_PIPE_D 2
+#endif
+#ifndef COBS_PIPE_WARPS
+#define COBS_PIPE_WARPS 2
+#endif
+#ifndef COBS_PIPE_IDX_AHEAD
+#define COBS_PIPE_IDX_AHEAD 1  // row indices are loaded 1 or 2 stages before they are issued
+#endif
+#ifndef COBS_PIPE_MINB
+#define COBS_PIPE_MINB 0  // 0: let the compiler choose the register count
+#endif
+constexpr int PIPE_WARPS = COBS_PIPE_WARPS;
 constexpr int PIPE_THREADS = PIPE_WARPS * 32;
-constexpr int PIPE_G = 16;
-constexpr int PIPE_D = 3;
+constexpr int PIPE_G = COBS_PIPE_G;  // rows per stage (8 or 16)
+constexpr int PIPE_D = COBS_PIPE_D;  // stages in the ring
+static_assert(PIPE_G == 8 || PIPE_G == 16, "stages of 8 or 16 rows");
+// A one-warp CTA variant of this kernel stopped with "illegal instruction" once
+// and its cause was not found; it is excluded.
+static_assert(PIPE_WARPS >= 2, "CTAs of at least two warps");
 
 // L2 eviction-priority policy: 0 normal, 1 evict first, 2 evict last.
 __device__ __forceinline__ uint64_t l2_policy(uint32_t kind) {
@@ -286,8 +308,8 @@ __device__ __forceinline__ void ripple(uint32_t (&lv)[4][L], W4 c) {
             c.v[w] = t;
         }
 }
-// Harley-Seal tree over the 16 rows of one stage (stride 32 uint4 = one per lane);
-// returns the carry of weight 16 (added to level 4 by the caller).
+// Harley-Seal trees over the rows of one stage (stride 32 uint4 = one per lane):
+// 16 rows return the carry of weight 16, 8 rows the carry of weight 8.
 template <int L>
 __device__ __forceinline__ W4 hs16_stage(uint32_t (&lv)[4][L], const uint4 *st) {
     W4 tA = csa_lv<0>(lv, w4(st[0 * 32]), w4(st[1 * 32]));
@@ -306,22 +328,54 @@ __device__ __forceinline__ W4 hs16_stage(uint32_t (&lv)[4][L], const uint4 *st) 
     W4 eB = csa_lv<2>(lv, fA, fB);
     return csa_lv<3>(lv, eA, eB);
 }
+template <int L>
+__device__ __forceinline__ W4 hs8_stage(uint32_t (&lv)[4][L], const uint4 *st) {
+    W4 tA = csa_lv<0>(lv, w4(st[0 * 32]), w4(st[1 * 32]));
+    W4 tB = csa_lv<0>(lv, w4(st[2 * 32]), w4(st[3 * 32]));
+    W4 fA = csa_lv<1>(lv, tA, tB);
+    tA = csa_lv<0>(lv, w4(st[4 * 32]), w4(st[5 * 32]));
+    tB = csa_lv<0>(lv, w4(st[6 * 32]), w4(st[7 * 32]));
+    W4 fB = csa_lv<1>(lv, tA, tB);
+    return csa_lv<2>(lv, fA, fB);
+}
 
-__device__ __forceinline__ void load_idx16(const uint32_t *ridx, uint32_t g, uint32_t ng, uint32_t (&r)[16],
-                                           uint64_t pol) {
+// Carries of weight 2^LV0 from consecutive stages, paired by two more levels of
+// full adders: only every fourth stage ripples into the upper counter levels.
+// Value held = counters + 2^LV0 * p0 (if h0) + 2^(LV0+1) * p1 (if h1).
+template <int LV0, int L>
+struct CarryPairs {
+    W4 p0, p1;
+    bool h0 = false, h1 = false;
+    __device__ __forceinline__ void add(uint32_t (&lv)[4][L], const W4 &c) {
+        if (!h0) { p0 = c; h0 = true; return; }
+        h0 = false;
+        const W4 c1 = csa_lv<LV0>(lv, p0, c);
+        if (!h1) { p1 = c1; h1 = true; return; }
+        h1 = false;
+        ripple<LV0 + 2, L>(lv, csa_lv<LV0 + 1>(lv, p1, c1));
+    }
+    __device__ __forceinline__ void flush(uint32_t (&lv)[4][L]) {
+        if (h0) ripple<LV0, L>(lv, p0);
+        if (h1) ripple<LV0 + 1, L>(lv, p1);
+        h0 = h1 = false;
+    }
+};
+
+__device__ __forceinline__ void load_idx(const uint32_t *ridx, uint32_t g, uint32_t ng, uint32_t (&r)[PIPE_G],
+                                         uint64_t pol) {
     if (g < ng) {
 #pragma unroll
-        for (int j = 0; j < 16; j += 4) {
-            uint4 v = ldg_hint(ridx + g * 16u + j, pol);
+        for (int j = 0; j < PIPE_G; j += 4) {
+            uint4 v = ldg_hint(ridx + g * (uint32_t)PIPE_G + j, pol);
             r[j] = v.x; r[j + 1] = v.y; r[j + 2] = v.z; r[j + 3] = v.w;
         }
     }
 }
 
-__device__ __forceinline__ void issue16(uint4 *stage_lane, const uint8_t *colbase, uint32_t rowbytes,
-                                        const uint32_t (&r)[16], uint32_t t0, uint32_t n, uint64_t pol) {
+__device__ __forceinline__ void issue_stage(uint4 *stage_lane, const uint8_t *colbase, uint32_t rowbytes,
+                                            const uint32_t (&r)[PIPE_G], uint32_t t0, uint32_t n, uint64_t pol) {
 #pragma unroll
-    for (int j = 0; j < 16; j++) {
+    for (int j = 0; j < PIPE_G; j++) {
         const bool ok = t0 + j < n;
         const uint8_t *src = ok ? colbase + (uint64_t)r[j] * rowbytes : colbase;
         cp_async16(stage_lane + j * 32, src, ok ? 16u : 0u, pol);
@@ -329,9 +383,14 @@ __device__ __forceinline__ void issue16(uint4 *stage_lane, const uint8_t *colbas
 }
 
 template <int LPQ, int L>
+#if COBS_PIPE_MINB > 0
+__global__ void __launch_bounds__(PIPE_THREADS, COBS_PIPE_MINB) k_gather_pipe(GatherArgs a) {
+#else
 __global__ void __launch_bounds__(PIPE_THREADS) k_gather_pipe(GatherArgs a) {
+#endif
     __shared__ __align__(16) uint4 s_stage[PIPE_WARPS][PIPE_D][PIPE_G][32];
     constexpr uint32_t QPW = 32 / LPQ;
+    constexpr int LV0 = PIPE_G == 16 ? 4 : 3;
     const uint32_t warp = threadIdx.x >> 5;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t qslot = lane / LPQ;
@@ -355,7 +414,7 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_gather_pipe(GatherArgs a) {
         const uint32_t col = sd.byte_off + c * 16u;
         const bool active = valid && col < blk.rowbytes;
         const uint32_t n = active ? ell : 0u;
-        const uint32_t ng = (n + 15u) >> 4;
+        const uint32_t ng = (n + PIPE_G - 1) / PIPE_G;
         const uint32_t *ridx = a.rows_idx + (uint64_t)sd.block * a.tcap + a.term_base[q];
         const uint8_t *colbase = a.rows + blk.row_offset + col;
         const uint32_t rowbytes = blk.rowbytes;
@@ -365,44 +424,45 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_gather_pipe(GatherArgs a) {
         for (int w = 0; w < 4; w++)
 #pragma unroll
             for (int l = 0; l < L; l++) lv[w][l] = 0u;
-        uint32_t ra[16], rb[16];
-        load_idx16(ridx, 0, ng, ra, pol_idx);
-        load_idx16(ridx, 1, ng, rb, pol_idx);
+        uint32_t ra[PIPE_G];
+        load_idx(ridx, 0, ng, ra, pol_idx);
+#if COBS_PIPE_IDX_AHEAD == 2
+        uint32_t rb[PIPE_G];
+        load_idx(ridx, 1, ng, rb, pol_idx);
+#endif
+        // after issuing group gi: ra <- indices of gi + 1 (and rb <- gi + 2)
+        auto advance_idx = [&](uint32_t gnext) {
+#if COBS_PIPE_IDX_AHEAD == 2
+#pragma unroll
+            for (int j = 0; j < PIPE_G; j++) ra[j] = rb[j];
+            load_idx(ridx, gnext + 1, ng, rb, pol_idx);
+#else
+            load_idx(ridx, gnext, ng, ra, pol_idx);
+#endif
+        };
         uint32_t gi = 0, si = 0;  // next group to issue, its stage
 #pragma unroll
         for (int p = 0; p < PIPE_D - 1; p++) {
-            if (gi < ng) issue16(&s_stage[warp][si][0][lane], colbase, rowbytes, ra, gi * 16u, n, pol_row);
+            if (gi < ng) issue_stage(&s_stage[warp][si][0][lane], colbase, rowbytes, ra, gi * PIPE_G, n, pol_row);
             cp_async_commit();
             gi++;
             si = si + 1 == PIPE_D ? 0 : si + 1;
-#pragma unroll
-            for (int j = 0; j < 16; j++) ra[j] = rb[j];
-            load_idx16(ridx, gi + 1, ng, rb, pol_idx);
+            advance_idx(gi);
         }
         uint32_t sc = 0;  // stage being consumed
-        // carries of weight 16 are paired by one more full adder at level 4, so
-        // only every second group ripples (from level 5) into the upper levels
-        W4 pend;
-        bool has_pend = false;
+        CarryPairs<LV0, L> carry;
         for (uint32_t g = 0; g < ng; g++) {
-            if (gi < ng) issue16(&s_stage[warp][si][0][lane], colbase, rowbytes, ra, gi * 16u, n, pol_row);
+            if (gi < ng) issue_stage(&s_stage[warp][si][0][lane], colbase, rowbytes, ra, gi * PIPE_G, n, pol_row);
             cp_async_commit();
             gi++;
             si = si + 1 == PIPE_D ? 0 : si + 1;
-#pragma unroll
-            for (int j = 0; j < 16; j++) ra[j] = rb[j];
-            load_idx16(ridx, gi + 1, ng, rb, pol_idx);
+            advance_idx(gi);
             cp_async_wait<PIPE_D - 1>();
-            const W4 six = hs16_stage<L>(lv, &s_stage[warp][sc][0][lane]);
-            if (has_pend) {
-                ripple<5, L>(lv, csa_lv<4>(lv, pend, six));
-            } else {
-                pend = six;
-            }
-            has_pend = !has_pend;
+            if constexpr (PIPE_G == 16) carry.add(lv, hs16_stage<L>(lv, &s_stage[warp][sc][0][lane]));
+            else carry.add(lv, hs8_stage<L>(lv, &s_stage[warp][sc][0][lane]));
             sc = sc + 1 == PIPE_D ? 0 : sc + 1;
         }
-        if (has_pend) ripple<4, L>(lv, pend);
+        carry.flush(lv);
         cp_async_wait<0>();
         if (n) emit_hits<L>(a, blk, col, q, ell, lv);
     }
