@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_hits_scan(HitsArgs a) {
     unsigned long long run = s_part[threadIdx.x] - sum;
     for (uint32_t q = q0; q < q1; q++) {
         a.hit_off[q] = run;
+        if (a.qcount[q] > SORT_SMEM_KEYS) a.big_list[atomicAdd(a.big_count, 1ULL)] = q;
         run += a.qcount[q];
         a.qcursor[q] = 0;
         uint32_t ell = a.ell[q];
@@ -95,8 +96,7 @@ __device__ __forceinline__ void unpack(const unsigned long long *src, uint32_t n
     }
 }
 
-// One CTA per query: sort its segment in shared memory when it fits, otherwise in
-// place in global memory (ping-pong with the scratch array).
+// One CTA per query with at most SORT_SMEM_KEYS hits: sort in shared memory.
 __global__ void __launch_bounds__(SORT_THREADS) k_hits_segsort(HitsArgs a) {
     __shared__ unsigned long long sA[SORT_SMEM_KEYS];
     __shared__ unsigned long long sB[SORT_SMEM_KEYS];
@@ -105,20 +105,10 @@ __global__ void __launch_bounds__(SORT_THREADS) k_hits_segsort(HitsArgs a) {
     if (total > a.hit_cap) return;  // the host re-runs with a larger capacity
     const uint64_t o = a.hit_off[q];
     const uint32_t n = (uint32_t)(a.hit_off[q + 1] - o);
-    if (n == 0) return;
-    if (n <= SORT_SMEM_KEYS) {
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) sA[i] = a.keys[o + i];
-        __syncthreads();
-        unsigned long long *src = sA, *dst = sB;
-        for (uint32_t w = 1; w < n; w <<= 1) {
-            merge_pass(src, dst, n, w);
-            __syncthreads();
-            unsigned long long *t = src; src = dst; dst = t;
-        }
-        unpack(src, n, o, a.out_ids, a.out_scores);
-        return;
-    }
-    unsigned long long *src = a.keys + o, *dst = a.tmp + o;
+    if (n == 0 || n > SORT_SMEM_KEYS) return;  // larger segments: k_hits_segsort_big
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) sA[i] = a.keys[o + i];
+    __syncthreads();
+    unsigned long long *src = sA, *dst = sB;
     for (uint32_t w = 1; w < n; w <<= 1) {
         merge_pass(src, dst, n, w);
         __syncthreads();
@@ -127,11 +117,85 @@ __global__ void __launch_bounds__(SORT_THREADS) k_hits_segsort(HitsArgs a) {
     unpack(src, n, o, a.out_ids, a.out_scores);
 }
 
+// Merge-path split of the output diagonal d of merging sorted A[0..na) and
+// B[0..nb) (unique keys): the number of A elements among the first d outputs.
+__device__ __forceinline__ uint32_t merge_split(const unsigned long long *A, uint32_t na,
+                                                const unsigned long long *B, uint32_t nb, uint32_t d) {
+    uint32_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (A[mid] < B[d - 1 - mid]) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+constexpr uint32_t BIG_SORT_THREADS = 1024;
+constexpr uint32_t BIG_SORT_CHUNK = 2048;
+
+// One CTA per query with more than SORT_SMEM_KEYS hits: sort chunks of
+// BIG_SORT_CHUNK keys in shared memory, then merge pairs of runs in global
+// memory; every thread merges a contiguous range of the output, found by a
+// merge-path binary search on its diagonal.
+__device__ void sort_big_segment(const HitsArgs &a, uint32_t q, unsigned long long *sA, unsigned long long *sB) {
+    const uint64_t o = a.hit_off[q];
+    const uint32_t n = (uint32_t)(a.hit_off[q + 1] - o);
+    unsigned long long *src = a.keys + o, *dst = a.tmp + o;
+    for (uint32_t c0 = 0; c0 < n; c0 += BIG_SORT_CHUNK) {
+        const uint32_t m = n - c0 < BIG_SORT_CHUNK ? n - c0 : BIG_SORT_CHUNK;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) sA[i] = src[c0 + i];
+        __syncthreads();
+        unsigned long long *x = sA, *y = sB;
+        for (uint32_t w = 1; w < m; w <<= 1) {
+            merge_pass(x, y, m, w);
+            __syncthreads();
+            unsigned long long *t = x; x = y; y = t;
+        }
+        for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) src[c0 + i] = x[i];
+    }
+    __syncthreads();
+    for (uint32_t w = BIG_SORT_CHUNK; w < n; w <<= 1) {
+        for (uint32_t p0 = 0; p0 < n; p0 += 2 * w) {
+            const uint32_t na = n - p0 < w ? n - p0 : w;
+            const uint32_t nb = n - p0 - na < w ? n - p0 - na : w;
+            const unsigned long long *A = src + p0, *B = src + p0 + na;
+            const uint32_t len = na + nb;
+            const uint32_t per = (len + blockDim.x - 1) / blockDim.x;
+            const uint32_t d0 = threadIdx.x * per < len ? threadIdx.x * per : len;
+            const uint32_t d1 = d0 + per < len ? d0 + per : len;
+            if (d0 < d1) {
+                uint32_t i = merge_split(A, na, B, nb, d0);
+                uint32_t j = d0 - i;
+                for (uint32_t d = d0; d < d1; d++) {
+                    const bool take_a = j >= nb || (i < na && A[i] < B[j]);
+                    dst[p0 + d] = take_a ? A[i++] : B[j++];
+                }
+            }
+        }
+        __syncthreads();
+        unsigned long long *t = src; src = dst; dst = t;
+    }
+    unpack(src, n, o, a.out_ids, a.out_scores);
+    __syncthreads();
+}
+
+// Fixed grid over the list of queries with more than SORT_SMEM_KEYS hits (made
+// by k_hits_scan).
+__global__ void __launch_bounds__(BIG_SORT_THREADS) k_hits_segsort_big(HitsArgs a) {
+    __shared__ unsigned long long sA[BIG_SORT_CHUNK];
+    __shared__ unsigned long long sB[BIG_SORT_CHUNK];
+    if (*a.hit_count > a.hit_cap) return;
+    const unsigned long long nbig = *a.big_count;
+    for (unsigned long long i = blockIdx.x; i < nbig; i += gridDim.x) sort_big_segment(a, a.big_list[i], sA, sB);
+}
+
 void launch_hits_finalize(const HitsArgs &a, cudaStream_t s) {
     if (a.n_queries == 0) return;
     k_hits_scan<<<1, SCAN_THREADS, 0, s>>>(a);
     k_hits_scatter<<<264, 256, 0, s>>>(a);
     k_hits_segsort<<<a.n_queries, SORT_THREADS, 0, s>>>(a);
+    const uint32_t grid = a.n_queries < 304 ? a.n_queries : 304;
+    k_hits_segsort_big<<<grid, BIG_SORT_THREADS, 0, s>>>(a);
 }
 
 }  // namespace cobs

@@ -556,6 +556,7 @@ static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n
     bp.total_slots = 0;
     bp.sum_npos = 0;
     bp.max_npos = 0;
+    bp.smem_slots = 16;
     for (uint64_t q = 0; q < n; q++) {
         if (h_off[q + 1] < h_off[q]) return set_error(COBS_ERR_ARG, "query offsets decrease at %llu", (unsigned long long)q);
         uint64_t len = h_off[q + 1] - h_off[q];
@@ -573,6 +574,7 @@ static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n
             bp.total_slots += sl;
         } else {
             bp.table_base[q] = 0;
+            bp.smem_slots = std::max<uint32_t>(bp.smem_slots, (uint32_t)sl);
         }
         bp.sum_npos += np;
         bp.max_npos = std::max(bp.max_npos, np);
@@ -600,6 +602,7 @@ static cobs_status ensure_buffers(cobs_engine *eng, const BatchPlan &bp) {
     CU(eng->minsc.ensure(n * 4));
     CU(eng->qcount.ensure(n * 4 + 64 * 8));  // qcount, then the counters (one memset clears both)
     CU(eng->qcursor.ensure(n * 4));
+    CU(eng->biglist.ensure(n * 4));
     CU(eng->hitoff.ensure((n + 1) * 8));
     CU(eng->rows_idx.ensure(std::max<uint64_t>(nb, 1) * h * bp.tcap * 4));
     CU(eng->codes.ensure(bp.tcap * 8));
@@ -659,6 +662,7 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
     ta.h = P.num_hashes;
     ta.kind = P.term_kind;
     ta.k = P.q;
+    ta.smem_slots = bp.smem_slots;
 
     if (flags & COBS_PLAIN) {
         // One query per kernel sequence: terms, zero scores, gather, threshold.
@@ -759,6 +763,8 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
     ha.tmp = eng->tmp.as<unsigned long long>();
     ha.out_ids = eng->out_ids.as<uint32_t>();
     ha.out_scores = eng->out_scores.as<uint32_t>();
+    ha.big_list = eng->biglist.as<uint32_t>();
+    ha.big_count = ctr + 15;  // cleared with the other counters
     launch_hits_finalize(ha, s);
     eng->stat_launches += 3;
     CU(cudaGetLastError());
@@ -779,12 +785,13 @@ static std::vector<uint64_t> graph_signature(cobs_engine *eng, const uint8_t *d_
                                              const uint16_t *d_thr) {
     const BatchPlan &bp = eng->bp;
     std::vector<uint64_t> sig = {bp.n, bp.tcap, bp.total_slots, (uint64_t)d_bytes, (uint64_t)d_off, (uint64_t)d_thr,
-                                 eng->hit_cap, eng->lanes_per_query, eng->ctas_per_sm, eng->l2_hints,
+                                 eng->hit_cap, eng->lanes_per_query, eng->ctas_per_sm, eng->l2_hints, bp.smem_slots,
                                  (uint64_t)eng->rows_idx.p, (uint64_t)eng->tables.p, (uint64_t)eng->raw_q.p,
                                  (uint64_t)eng->codes.p,
                                  (uint64_t)eng->plan.p, (uint64_t)eng->pin_plan.p, (uint64_t)eng->qcount.p,
                                  (uint64_t)eng->ell.p, (uint64_t)eng->minsc.p, (uint64_t)eng->qcursor.p,
                                  (uint64_t)eng->hitoff.p, (uint64_t)eng->raw_key.p, (uint64_t)eng->keys.p,
+                                 (uint64_t)eng->biglist.p,
                                  (uint64_t)eng->tmp.p, (uint64_t)eng->out_ids.p, (uint64_t)eng->out_scores.p,
                                  (uint64_t)eng->pin_count.p, (uint64_t)eng->slices.p, eng->n_slices};
     for (const auto &c : bp.classes) {

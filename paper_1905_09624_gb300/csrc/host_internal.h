@@ -76,6 +76,7 @@ struct BatchPlan {
     };
     std::vector<Class> classes;
     uint64_t tcap = 0, total_slots = 0, sum_npos = 0, max_npos = 0;
+    uint32_t smem_slots = 16;  // largest distinct set of the batch kept in shared memory
 };
 
 struct ResultStore;
@@ -115,7 +116,7 @@ struct cobs_engine {
     // per batch
     cobs::DevBuf qbytes, qoff, thr;          // staging of host queries
     cobs::DevBuf plan;                        // term_base | table_base | order
-    cobs::DevBuf ell, minsc, qcount, qcursor, hitoff;
+    cobs::DevBuf ell, minsc, qcount, qcursor, hitoff, biglist;
     cobs::DevBuf counters;                    // [0] hit count, [1..] work counters
     cobs::DevBuf rows_idx, tables, codes;
     cobs::DevBuf raw_q, raw_key, keys, tmp, out_ids, out_scores;

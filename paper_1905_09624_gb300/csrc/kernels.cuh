@@ -8,11 +8,12 @@
 namespace cobs {
 
 // Query-term table: shared-memory slots per CTA before the set spills to global memory.
-constexpr uint32_t TERMS_SMEM_SLOTS = 4096;   // 32 KB
+constexpr uint32_t TERMS_SMEM_SLOTS = 4096;   // 32 KB: largest distinct set kept in shared memory
 constexpr uint32_t TERMS_THREADS = 256;
 constexpr uint32_t TERMS_SEG = 8;             // windows rolled by one thread per round
 constexpr uint32_t TERMS_BUCKET_BITS = 6;     // terms are emitted in 64 row buckets per block
 constexpr uint32_t TERMS_BUCKETS = 1u << TERMS_BUCKET_BITS;
+constexpr uint32_t TERMS_BLOCKS_PER_PASS = 4;   // blocks whose rows one pass over the terms computes
 
 struct TermsArgs {
     const uint8_t *bytes;          // queries concatenated
@@ -27,6 +28,7 @@ struct TermsArgs {
     const DevBlock *blocks;
     uint32_t n_blocks, h, kind, k;
     uint32_t q0;                   // first query handled by blockIdx.x == 0
+    uint32_t smem_slots;           // sets of up to this many slots live in shared memory (<= TERMS_SMEM_SLOTS)
 };
 void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s);
 
@@ -120,6 +122,8 @@ struct HitsArgs {
     unsigned long long *tmp;       // sort scratch (same size)
     uint32_t *out_ids;
     uint32_t *out_scores;
+    uint32_t *big_list;            // scratch, n_queries entries: queries with many hits
+    unsigned long long *big_count; // zeroed before the launch
 };
 void launch_hits_finalize(const HitsArgs &a, cudaStream_t s);
 

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     const uint32_t k = a.k;
     const uint64_t npos = len >= k ? len - k + 1 : 0;
     const uint32_t cap = (uint32_t)set_slots(npos);
-    const bool in_smem = cap <= TERMS_SMEM_SLOTS;
+    const bool in_smem = cap <= a.smem_slots;
     unsigned long long *table = in_smem ? s_table : a.tables + a.table_base[q];
 
     for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) table[i] = EMPTY_KEY;
@@ -130,40 +130,70 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     // sort by the top bits of the hash-0 row).  Scores do not depend on the order
     // of the terms; bucketed order makes all warps of the gather sweep the rows of
     // a slice together, so the rows in use at any moment form a narrow band.
-    __shared__ uint32_t s_hist[TERMS_BUCKETS];
-    for (uint32_t b = 0; b < a.n_blocks; b++) {
-        const DevBlock blk = a.blocks[b];
-        const int lg = 32 - __clz(blk.w > 1 ? blk.w - 1 : 0);   // bits of the largest row
-        const uint32_t shift = lg > TERMS_BUCKET_BITS ? (uint32_t)(lg - TERMS_BUCKET_BITS) : 0u;
-        for (uint32_t i = threadIdx.x; i < TERMS_BUCKETS; i += blockDim.x) s_hist[i] = 0;
+    // Blocks are handled TERMS_BLOCKS_PER_PASS at a time, so every term is hashed
+    // once per pass whatever the number of blocks.
+    constexpr uint32_t BP = TERMS_BLOCKS_PER_PASS;
+    __shared__ uint32_t s_hist[BP * TERMS_BUCKETS];
+    __shared__ uint32_t s_shift[BP];
+    const uint32_t warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    for (uint32_t b0 = 0; b0 < a.n_blocks; b0 += BP) {
+        const uint32_t nbp = a.n_blocks - b0 < BP ? a.n_blocks - b0 : BP;
+        for (uint32_t i = threadIdx.x; i < nbp * TERMS_BUCKETS; i += blockDim.x) s_hist[i] = 0;
+        if (threadIdx.x < nbp) {
+            const uint32_t w = a.blocks[b0 + threadIdx.x].w;
+            const int lg = 32 - __clz(w > 1 ? w - 1 : 0);  // bits of the largest row
+            s_shift[threadIdx.x] = lg > (int)TERMS_BUCKET_BITS ? (uint32_t)(lg - TERMS_BUCKET_BITS) : 0u;
+        }
         __syncthreads();
         each_distinct([&](uint64_t, uint64_t h0) {
-            const uint32_t r0 = barrett_mod(h0, blk.barrett_m, blk.w);
-            atomicAdd(&s_hist[r0 >> shift], 1u);
+#pragma unroll
+            for (uint32_t j = 0; j < BP; j++) {
+                if (j < nbp) {
+                    const DevBlock blk = a.blocks[b0 + j];
+                    const uint32_t r0 = barrett_mod(h0, blk.barrett_m, blk.w);
+                    atomicAdd(&s_hist[j * TERMS_BUCKETS + (r0 >> s_shift[j])], 1u);
+                }
+            }
         });
         __syncthreads();
-        if (threadIdx.x < 32) {  // exclusive scan of the bucket counts by one warp
+        for (uint32_t j = warp; j < nbp; j += n_warps) {  // exclusive scan per block, one warp each
+            uint32_t *hj = s_hist + j * TERMS_BUCKETS;
             uint32_t carry = 0;
             for (uint32_t c0 = 0; c0 < TERMS_BUCKETS; c0 += 32) {
-                const uint32_t v = s_hist[c0 + lane];
+                const uint32_t v = hj[c0 + lane];
                 uint32_t x = v;
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
                     const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
                     if ((int)lane >= d) x += y;
                 }
-                s_hist[c0 + lane] = carry + x - v;
+                hj[c0 + lane] = carry + x - v;
                 carry += __shfl_sync(0xffffffffu, x, 31);
             }
         }
         __syncthreads();
         each_distinct([&](uint64_t code, uint64_t h0) {
-            const uint32_t r0 = barrett_mod(h0, blk.barrett_m, blk.w);
-            const uint32_t pos = atomicAdd(&s_hist[r0 >> shift], 1u);
-            a.rows_idx[(uint64_t)(b * a.h) * a.tcap + base + pos] = r0;
-            for (uint32_t i2 = 1; i2 < a.h; i2++)
-                a.rows_idx[(uint64_t)(b * a.h + i2) * a.tcap + base + pos] =
-                    barrett_mod(xxh64_u64(code, i2), blk.barrett_m, blk.w);
+            uint32_t pos[BP];
+#pragma unroll
+            for (uint32_t j = 0; j < BP; j++) {
+                if (j < nbp) {
+                    const DevBlock blk = a.blocks[b0 + j];
+                    const uint32_t r0 = barrett_mod(h0, blk.barrett_m, blk.w);
+                    pos[j] = atomicAdd(&s_hist[j * TERMS_BUCKETS + (r0 >> s_shift[j])], 1u);
+                    a.rows_idx[(uint64_t)((b0 + j) * a.h) * a.tcap + base + pos[j]] = r0;
+                }
+            }
+            for (uint32_t i2 = 1; i2 < a.h; i2++) {
+                const uint64_t hv = xxh64_u64(code, i2);
+#pragma unroll
+                for (uint32_t j = 0; j < BP; j++) {
+                    if (j < nbp) {
+                        const DevBlock blk = a.blocks[b0 + j];
+                        a.rows_idx[(uint64_t)((b0 + j) * a.h + i2) * a.tcap + base + pos[j]] =
+                            barrett_mod(hv, blk.barrett_m, blk.w);
+                    }
+                }
+            }
         });
         __syncthreads();
     }
@@ -172,11 +202,13 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
 void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s) {
     if (n_queries == 0) return;
     static bool attr_set = false;
-    const int dyn = TERMS_SMEM_SLOTS * sizeof(unsigned long long);
     if (!attr_set) {
-        cudaFuncSetAttribute(k_query_terms, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        cudaFuncSetAttribute(k_query_terms, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(TERMS_SMEM_SLOTS * sizeof(unsigned long long)));
         attr_set = true;
     }
+    // shared memory sized to the largest set of the launch that is kept on chip
+    const size_t dyn = (size_t)a.smem_slots * sizeof(unsigned long long);
     k_query_terms<<<n_queries, TERMS_THREADS, dyn, s>>>(a);
 }
 
