@@ -209,6 +209,20 @@ def run_reference(args):
     return 0
 
 
+def aggregate_over_ranks(seconds, units, dist=None, device="cpu"):
+    """Whole-job throughput of N independent replicas: the slowest rank's time
+    (max over ranks) and the units all ranks processed (sum).  With one process
+    (dist None) it is (seconds, units)."""
+    if dist is None:
+        return float(seconds), float(units)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # -------------------------------------------------------------------- serve
 def run_serve(dix, wl, rates, seconds, verify_oracle=None):
     """Poisson arrivals (cfg5 recipe on the given index) submitted at their
@@ -374,16 +388,7 @@ def run_gpu(args):
     barrier()
     t_wall1 = time.time()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    T = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([T], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        T = float(t.item())
-        u = torch.tensor([terms_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        terms_all = float(u.item())
-    else:
-        terms_all = float(terms_total)
+    T, terms_all = aggregate_over_ranks(sum(step_ms) / 1e3, terms_total, dist, device="cuda")
     value = terms_all / T
 
     phases = {k: st[k] for k in ("ms_terms", "ms_gather", "ms_hits", "ms_total")}

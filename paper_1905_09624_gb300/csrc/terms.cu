@@ -4,11 +4,11 @@
 // i < h its row XXH64(term, i) mod w_b (Sec. 2.2), written as a u32 row index.
 //
 // The query is processed in rounds of TERMS_ROUND windows.  Each round stages
-// its bytes in shared memory (coalesced loads), then
-//   phase A: every thread rolls the 2-bit codes of TERMS_SEG consecutive windows
-//            and writes the window codes to shared memory;
-//   phase B: every thread takes one window at a time: hash, set insertion, and
-//            the warp-aggregated append of fresh terms with their row indices.
+// its bytes in shared memory (coalesced loads); every thread then rolls the
+// 2-bit codes of TERMS_SEG consecutive windows and, as each window completes,
+// hashes it, inserts it into the set and appends it to the distinct list when it
+// is new (warp-aggregated).  The list holds hash 0 when h == 1 (all the row pass
+// needs), else the code.  A final pass writes the rows in row-bucket order.
 #include "kernels.cuh"
 
 namespace cobs {
@@ -19,8 +19,7 @@ constexpr uint32_t TERMS_STAGE_BYTES = TERMS_ROUND + 32;      // + k - 1 <= 31 b
 __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     extern __shared__ unsigned long long s_table[];
     __shared__ __align__(16) uint8_t s_bytes[TERMS_STAGE_BYTES];
-    __shared__ unsigned long long s_code[TERMS_ROUND];
-    __shared__ uint8_t s_valid[TERMS_ROUND];
+    __shared__ unsigned long long s_list[TERMS_ROUND];  // distinct list of an on-chip set
     __shared__ uint32_t s_ell;
     __shared__ uint32_t s_has_empty;
 
@@ -30,46 +29,39 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     const uint32_t k = a.k;
     const uint64_t npos = len >= k ? len - k + 1 : 0;
     const uint32_t cap = (uint32_t)set_slots(npos);
+    // a set that fits on chip holds at most TERMS_ROUND distinct terms (one round)
     const bool in_smem = cap <= a.smem_slots;
     unsigned long long *table = in_smem ? s_table : a.tables + a.table_base[q];
+    const uint64_t base = a.term_base[q];
+    unsigned long long *list = in_smem ? s_list : a.codes + base;
 
     for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) table[i] = EMPTY_KEY;
     if (threadIdx.x == 0) { s_ell = 0; s_has_empty = 0; }
 
     const uint8_t *src = a.bytes + off0;
     const uint64_t mask = kmer_mask(k);
-    const uint64_t base = a.term_base[q];
     const uint32_t lane = threadIdx.x & 31u;
 
     for (uint64_t r0 = 0; r0 < npos; r0 += TERMS_ROUND) {
         const uint32_t rn = (uint32_t)(npos - r0 < TERMS_ROUND ? npos - r0 : TERMS_ROUND);
         const uint32_t nbytes = rn + k - 1;
-        __syncthreads();  // previous round finished with s_bytes / s_code (and the table init)
+        __syncthreads();  // previous round finished with s_bytes (and the table init)
         for (uint32_t i = threadIdx.x; i < nbytes; i += blockDim.x) s_bytes[i] = src[r0 + i];
         __syncthreads();
-        // phase A: rolling codes of windows [w0, w1)
-        {
-            const uint32_t w0 = threadIdx.x * TERMS_SEG;
-            const uint32_t w1 = w0 + TERMS_SEG < rn ? w0 + TERMS_SEG : rn;
-            if (w0 < w1) {
-                Roller r;
-                roll_init(r);
-                for (uint32_t i = w0; i < w1 + k - 1; i++) {
-                    uint64_t code = 0;
-                    bool term = roll_push(r, s_bytes[i], a.kind, k, mask, &code);
-                    if (i + 1 >= w0 + k) {  // the window ending at byte i starts at i + 1 - k >= w0
-                        const uint32_t w = i + 1 - k;
-                        s_code[w] = code;
-                        s_valid[w] = term ? 1 : 0;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // phase B: one window per thread and iteration (uniform trip count per warp)
-        for (uint32_t w = threadIdx.x; w < ((rn + 31u) & ~31u); w += blockDim.x) {
-            const bool term = w < rn && s_valid[w];
-            const uint64_t code = term ? s_code[w] : 0;
+        // windows [w0, w1) of this thread; bytes [w0, w1 + k - 1) feed them
+        const uint32_t w0 = threadIdx.x * TERMS_SEG;
+        const uint32_t w1 = w0 + TERMS_SEG < rn ? w0 + TERMS_SEG : rn;
+        const uint32_t ie = w1 > w0 ? w1 + k - 1 : w0;
+        // warps whose lanes all lie past the round's windows skip the loop together
+        if (__all_sync(0xffffffffu, w0 >= w1)) continue;
+        Roller r;
+        roll_init(r);
+        // the same trip count in every lane of the warp, for the warp-level append
+        for (uint32_t step = 0; step < TERMS_SEG + 31; step++) {
+            const uint32_t i = w0 + step;
+            uint64_t code = 0;
+            bool term = false;
+            if (i < ie) term = roll_push(r, s_bytes[i], a.kind, k, mask, &code) && i + 1 >= w0 + k;
             bool fresh = false;
             uint64_t h0 = 0;
             if (term) {
@@ -83,50 +75,23 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
                 const uint32_t leader = __ffs(m) - 1;
                 if (lane == leader) slot0 = atomicAdd(&s_ell, (uint32_t)__popc(m));
                 slot0 = __shfl_sync(0xffffffffu, slot0, leader);
-                // a set in shared memory is compacted after the rounds; a spilled set
-                // keeps a compact list instead (the hash-0 value when h == 1, which is
-                // all phase C needs, else the code)
-                if (fresh && !in_smem)
-                    a.codes[base + slot0 + __popc(m & ((1u << lane) - 1u))] = a.h == 1 ? h0 : code;
+                if (fresh) list[slot0 + __popc(m & ((1u << lane) - 1u))] = a.h == 1 ? h0 : code;
             }
         }
     }
     __syncthreads();
     const uint32_t ell = s_ell;
     if (threadIdx.x == 0) a.ell[q] = ell;
-    // A set in shared memory holds at most TERMS_ROUND codes (one round): compact
-    // it into the window-code buffer, which is free now.
-    if (in_smem) {
-        __shared__ uint32_t s_fill;
-        if (threadIdx.x == 0) s_fill = 0;
-        __syncthreads();
-        for (uint32_t i0 = 0; i0 < cap; i0 += blockDim.x) {
-            const uint32_t i = i0 + threadIdx.x;
-            const uint64_t c = i < cap ? table[i] : EMPTY_KEY;
-            const bool occ = c != EMPTY_KEY;
-            const uint32_t m = __ballot_sync(0xffffffffu, occ);
-            uint32_t p0 = 0;
-            if (m) {
-                const uint32_t leader = __ffs(m) - 1;
-                if (lane == leader) p0 = atomicAdd(&s_fill, (uint32_t)__popc(m));
-                p0 = __shfl_sync(0xffffffffu, p0, leader);
-            }
-            if (occ) s_code[p0 + __popc(m & ((1u << lane) - 1u))] = a.h == 1 ? xxh64_u64(c, 0) : c;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0 && s_has_empty) s_code[s_fill] = a.h == 1 ? xxh64_u64(EMPTY_KEY, 0) : EMPTY_KEY;
-        __syncthreads();
-    }
     // every distinct term once, spread over the threads: f(code, hash 0); the code
     // is only meaningful (and only used) when h > 1
     auto each_distinct = [&](auto &&f) {
         for (uint32_t t = threadIdx.x; t < ell; t += blockDim.x) {
-            const uint64_t key = in_smem ? (uint64_t)s_code[t] : (uint64_t)a.codes[base + t];
+            const uint64_t key = list[t];
             f(key, a.h == 1 ? key : xxh64_u64(key, 0));
         }
     };
 
-    // phase C: per block, the distinct terms' rows in row-bucket order (a counting
+    // Row pass: per block, the distinct terms' rows in row-bucket order (a counting
     // sort by the top bits of the hash-0 row).  Scores do not depend on the order
     // of the terms; bucketed order makes all warps of the gather sweep the rows of
     // a slice together, so the rows in use at any moment form a narrow band.
