@@ -4,11 +4,15 @@
 // i < h its row XXH64(term, i) mod w_b (Sec. 2.2), written as a u32 row index.
 //
 // The query is processed in rounds of TERMS_ROUND windows.  Each round stages
-// its bytes in shared memory (coalesced loads); every thread then rolls the
-// 2-bit codes of TERMS_SEG consecutive windows and, as each window completes,
-// hashes it, inserts it into the set and appends it to the distinct list when it
-// is new (warp-aggregated).  The list holds hash 0 when h == 1 (all the row pass
-// needs), else the code.  A final pass writes the rows in row-bucket order.
+// its bytes in shared memory (coalesced loads) and, for DNA, packs them into a
+// 2-bit base stream and a mask of non-ACGT bytes, 16 bases per word.  Every
+// thread then takes one window at a time: its k bases are a funnel shift of
+// three packed words, its validity a shift of the mask, its reverse complement a
+// bit reversal of the complemented code with the bits of each base swapped back.
+// The window is hashed, inserted into the set and appended to the distinct list
+// when it is new (warp-aggregated).  The list holds hash 0 when h == 1 (all the
+// row pass needs), else the code.  A final pass writes the rows in row-bucket
+// order.
 #include "kernels.cuh"
 
 namespace cobs {
@@ -20,6 +24,8 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     extern __shared__ unsigned long long s_table[];
     __shared__ __align__(16) uint8_t s_bytes[TERMS_STAGE_BYTES];
     __shared__ unsigned long long s_list[TERMS_ROUND];  // distinct list of an on-chip set
+    __shared__ uint32_t s_pk[TERMS_STAGE_BYTES / 16 + 3];   // 2-bit bases, 16 per word
+    __shared__ uint16_t s_inv[TERMS_STAGE_BYTES / 16 + 3];  // non-ACGT bytes, 16 per word
     __shared__ uint32_t s_ell;
     __shared__ uint32_t s_has_empty;
 
@@ -42,26 +48,65 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     const uint64_t mask = kmer_mask(k);
     const uint32_t lane = threadIdx.x & 31u;
 
+    const bool dna = a.kind != KIND_BYTES;
     for (uint64_t r0 = 0; r0 < npos; r0 += TERMS_ROUND) {
         const uint32_t rn = (uint32_t)(npos - r0 < TERMS_ROUND ? npos - r0 : TERMS_ROUND);
         const uint32_t nbytes = rn + k - 1;
         __syncthreads();  // previous round finished with s_bytes (and the table init)
         for (uint32_t i = threadIdx.x; i < nbytes; i += blockDim.x) s_bytes[i] = src[r0 + i];
         __syncthreads();
-        // windows [w0, w1) of this thread; bytes [w0, w1 + k - 1) feed them
-        const uint32_t w0 = threadIdx.x * TERMS_SEG;
-        const uint32_t w1 = w0 + TERMS_SEG < rn ? w0 + TERMS_SEG : rn;
-        const uint32_t ie = w1 > w0 ? w1 + k - 1 : w0;
-        // warps whose lanes all lie past the round's windows skip the loop together
-        if (__all_sync(0xffffffffu, w0 >= w1)) continue;
-        Roller r;
-        roll_init(r);
-        // the same trip count in every lane of the warp, for the warp-level append
-        for (uint32_t step = 0; step < TERMS_SEG + 31; step++) {
-            const uint32_t i = w0 + step;
+        if (dna) {
+            // pack 16 bases per word: 2-bit codes, first base most significant, and
+            // a 16-bit mask of the bytes that are not A, C, G or T (first base = MSB)
+            const uint32_t nwords = (nbytes + 15) >> 4;
+            for (uint32_t t = threadIdx.x; t < nwords + 2; t += blockDim.x) {
+                uint32_t pk = 0, inv = 0;
+                if (t < nwords) {
+#pragma unroll
+                    for (uint32_t j = 0; j < 16; j++) {
+                        const uint32_t i = t * 16 + j;
+                        const uint32_t c = i < nbytes ? s_bytes[i] : 0u;
+                        const bool ok = c == 'A' || c == 'C' || c == 'G' || c == 'T';
+                        uint32_t b = (c >> 1) & 3u;  // A, C, T, G -> 0, 1, 2, 3
+                        b ^= b >> 1;                 // -> A 0, C 1, G 2, T 3
+                        pk = (pk << 2) | (ok ? b : 0u);
+                        inv = (inv << 1) | (ok ? 0u : 1u);
+                    }
+                }
+                s_pk[t] = pk;
+                s_inv[t] = (uint16_t)inv;
+            }
+            __syncthreads();
+        }
+        // one window per thread and iteration; every lane of a warp runs the same
+        // number of iterations, for the warp-level append
+        for (uint32_t p = threadIdx.x; p < ((rn + 31u) & ~31u); p += blockDim.x) {
             uint64_t code = 0;
             bool term = false;
-            if (i < ie) term = roll_push(r, s_bytes[i], a.kind, k, mask, &code) && i + 1 >= w0 + k;
+            if (p < rn) {
+                if (dna) {
+                    const uint32_t w = p >> 4, o = p & 15u;
+                    // bases p .. p + k - 1: the top 2k bits of words w, w+1, w+2 shifted by 2o
+                    const uint64_t A = ((uint64_t)s_pk[w] << 32) | s_pk[w + 1];
+                    const uint64_t hi = o ? (A << (2 * o)) | (s_pk[w + 2] >> (32 - 2 * o)) : A;
+                    const uint64_t fwd = hi >> (64 - 2 * k);
+                    const uint64_t X = ((uint64_t)s_inv[w] << 32) | ((uint64_t)s_inv[w + 1] << 16) | s_inv[w + 2];
+                    term = ((X << (16 + o)) >> (64 - k)) == 0;
+                    if (a.kind == KIND_DNA_CANONICAL) {
+                        // reverse complement: complement, reverse the 2-bit groups
+                        uint64_t x = __brevll(~(fwd << (64 - 2 * k)));
+                        x = ((x >> 1) & 0x5555555555555555ULL) | ((x & 0x5555555555555555ULL) << 1);
+                        const uint64_t rc = x & mask;
+                        code = rc < fwd ? rc : fwd;
+                    } else {
+                        code = fwd;
+                    }
+                } else {
+                    // q bytes little-endian
+                    for (uint32_t j = 0; j < k; j++) code |= (uint64_t)s_bytes[p + j] << (8 * j);
+                    term = true;
+                }
+            }
             bool fresh = false;
             uint64_t h0 = 0;
             if (term) {
