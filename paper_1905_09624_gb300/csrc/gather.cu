@@ -374,11 +374,16 @@ __device__ __forceinline__ void load_idx(const uint32_t *ridx, uint32_t g, uint3
 
 __device__ __forceinline__ void issue_stage(uint4 *stage_lane, const uint8_t *colbase, uint32_t rowbytes,
                                             const uint32_t (&r)[PIPE_G], uint32_t t0, uint32_t n, uint64_t pol) {
+    if (t0 + PIPE_G <= n) {  // a full group: no per-row predicates
+#pragma unroll
+        for (int j = 0; j < PIPE_G; j++) cp_async16(stage_lane + j * 32, colbase + (uint64_t)r[j] * rowbytes, 16u, pol);
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < PIPE_G; j++) {
         const bool ok = t0 + j < n;
         const uint8_t *src = ok ? colbase + (uint64_t)r[j] * rowbytes : colbase;
-        cp_async16(stage_lane + j * 32, src, ok ? 16u : 0u, pol);
+        cp_async16(stage_lane + j * 32, src, ok ? 16u : 0u, pol);  // past the terms: zero fill
     }
 }
 
