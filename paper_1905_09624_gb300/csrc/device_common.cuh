@@ -103,6 +103,64 @@ __device__ __forceinline__ bool roll_push(Roller &r, uint8_t c, uint32_t kind, u
     return true;
 }
 
+// ------------------------------------------------- packed base streams
+// A staged run of DNA bytes packed 16 bases per word: pk holds the 2-bit codes,
+// first base most significant; inv marks bytes that are not A, C, G or T (first
+// base = most significant bit).  Arrays need ceil(nbytes / 16) + 2 words.
+// Cooperative: all threads of the CTA call it; the caller synchronises after.
+__device__ __forceinline__ void pack_bases(const uint8_t *s_bytes, uint32_t nbytes, uint32_t *s_pk,
+                                           uint16_t *s_inv) {
+    const uint32_t nwords = (nbytes + 15) >> 4;
+    for (uint32_t t = threadIdx.x; t < nwords + 2; t += blockDim.x) {
+        uint32_t pk = 0, inv = 0;
+        if (t < nwords) {
+#pragma unroll
+            for (uint32_t j = 0; j < 16; j++) {
+                const uint32_t i = t * 16 + j;
+                const uint32_t c = i < nbytes ? s_bytes[i] : 0u;
+                const bool ok = c == 'A' || c == 'C' || c == 'G' || c == 'T';
+                uint32_t b = (c >> 1) & 3u;  // A, C, T, G -> 0, 1, 2, 3
+                b ^= b >> 1;                 // -> A 0, C 1, G 2, T 3
+                pk = (pk << 2) | (ok ? b : 0u);
+                inv = (inv << 1) | (ok ? 0u : 1u);
+            }
+        }
+        s_pk[t] = pk;
+        s_inv[t] = (uint16_t)inv;
+    }
+}
+
+// The k-mer starting at base p of a packed run (k <= 32): its k bases are the
+// top 2k bits of words w, w+1, w+2 shifted by 2o, its validity a shift of the
+// mask, its reverse complement a bit reversal of the complemented code with the
+// two bits of each base swapped back.  Returns false for a window with a
+// non-ACGT byte.
+__device__ __forceinline__ bool packed_kmer(const uint32_t *s_pk, const uint16_t *s_inv, uint32_t p, uint32_t k,
+                                            bool canonical, uint64_t mask, uint64_t *code) {
+    const uint32_t w = p >> 4, o = p & 15u;
+    const uint64_t A = ((uint64_t)s_pk[w] << 32) | s_pk[w + 1];
+    const uint64_t hi = o ? (A << (2 * o)) | (s_pk[w + 2] >> (32 - 2 * o)) : A;
+    const uint64_t fwd = hi >> (64 - 2 * k);
+    const uint64_t X = ((uint64_t)s_inv[w] << 32) | ((uint64_t)s_inv[w + 1] << 16) | s_inv[w + 2];
+    if (((X << (16 + o)) >> (64 - k)) != 0) return false;
+    if (canonical) {
+        uint64_t x = __brevll(~(fwd << (64 - 2 * k)));
+        x = ((x >> 1) & 0x5555555555555555ULL) | ((x & 0x5555555555555555ULL) << 1);
+        const uint64_t rc = x & mask;
+        *code = rc < fwd ? rc : fwd;
+    } else {
+        *code = fwd;
+    }
+    return true;
+}
+
+// The byte q-gram starting at byte p (q <= 8 bytes, little-endian).
+__device__ __forceinline__ uint64_t bytes_qgram(const uint8_t *s_bytes, uint32_t p, uint32_t q) {
+    uint64_t v = 0;
+    for (uint32_t j = 0; j < q; j++) v |= (uint64_t)s_bytes[p + j] << (8 * j);
+    return v;
+}
+
 // Open-addressing set of 64-bit codes; EMPTY marks a free slot.  The value
 // EMPTY itself (possible only for 8-byte q-grams of 0xFF bytes) is tracked by a
 // separate flag by the caller.

@@ -154,7 +154,7 @@ static cobs_status build_impl(const cobs_params *P, const uint8_t *d_docs, const
                                                       (unsigned long long)d);
         uint64_t len = h_off[d + 1] - h_off[d];
         npos[d] = len >= k ? len - k + 1 : 0;
-        for (uint64_t p = 0; p < npos[d]; p += BUILD_CHUNK) {
+        for (uint64_t p = 0; p < npos[d]; p += COUNT_CHUNK) {
             chunk_doc.push_back((uint32_t)d);
             chunk_p0.push_back(p);
         }
@@ -265,6 +265,26 @@ static cobs_status build_impl(const cobs_params *P, const uint8_t *d_docs, const
         cudaMemcpyAsync(ddocblk.p, doc_block.data(), n_docs * 4, cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(ddoccol.p, doc_col.data(), n_docs * 4, cudaMemcpyHostToDevice, s);
     }
+    // Bit-setting work in column order (block, sorted position): CTAs that run
+    // together set bits of neighbouring columns, i.e. of the same 32-bit words of
+    // every row, so the words being updated stay in L2.
+    std::vector<uint32_t> sb_doc;
+    std::vector<uint64_t> sb_p0;
+    for (uint64_t pos = 0; pos < n_docs; pos++) {
+        const uint64_t d = dix->perm[pos];
+        for (uint64_t p = 0; p < npos[d]; p += SETBITS_CHUNK) {
+            sb_doc.push_back((uint32_t)d);
+            sb_p0.push_back(p);
+        }
+    }
+    const uint64_t n_sb = sb_doc.size();
+    if (n_sb > 0x7FFFFFFFULL) return fail(set_error(COBS_ERR_ARG, "documents too large for one build"));
+    if ((ce = dchunk_doc.ensure(n_sb * 4)) != cudaSuccess || (ce = dchunk_p0.ensure(n_sb * 8)) != cudaSuccess)
+        return fail(set_error(COBS_ERR_OOM, "build chunk lists: %s", cudaGetErrorString(ce)));
+    if (n_sb) {
+        cudaMemcpyAsync(dchunk_doc.p, sb_doc.data(), n_sb * 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(dchunk_p0.p, sb_p0.data(), n_sb * 8, cudaMemcpyHostToDevice, s);
+    }
     SetBitsArgs sa{};
     sa.docs = d_docs;
     sa.doc_off = d_off;
@@ -277,7 +297,7 @@ static cobs_status build_impl(const cobs_params *P, const uint8_t *d_docs, const
     sa.kind = P->term_kind;
     sa.k = k;
     sa.h = P->num_hashes;
-    launch_doc_setbits(sa, (uint32_t)n_chunks, s);
+    launch_doc_setbits(sa, (uint32_t)n_sb, s);
     if ((ce = cudaGetLastError()) != cudaSuccess || (ce = cudaStreamSynchronize(s)) != cudaSuccess)
         return fail(set_error(COBS_ERR_CUDA, "build kernels: %s", cudaGetErrorString(ce)));
     *out = dix;

@@ -128,7 +128,11 @@ struct HitsArgs {
 void launch_hits_finalize(const HitsArgs &a, cudaStream_t s);
 
 // Device build: distinct-term counts, Bloom bit-setting.
-constexpr uint32_t BUILD_CHUNK = 16384;  // positions per CTA
+// Windows per CTA.  Small counting chunks put many CTAs on each document, so
+// few documents' sets are live at once; bit-setting runs in column order, so
+// CTAs that run together update the same words.
+constexpr uint32_t COUNT_CHUNK = 4096;
+constexpr uint32_t SETBITS_CHUNK = 8192;
 constexpr uint32_t BUILD_THREADS = 256;
 struct CountArgs {
     const uint8_t *docs;

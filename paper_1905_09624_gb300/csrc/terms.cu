@@ -56,26 +56,7 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
         for (uint32_t i = threadIdx.x; i < nbytes; i += blockDim.x) s_bytes[i] = src[r0 + i];
         __syncthreads();
         if (dna) {
-            // pack 16 bases per word: 2-bit codes, first base most significant, and
-            // a 16-bit mask of the bytes that are not A, C, G or T (first base = MSB)
-            const uint32_t nwords = (nbytes + 15) >> 4;
-            for (uint32_t t = threadIdx.x; t < nwords + 2; t += blockDim.x) {
-                uint32_t pk = 0, inv = 0;
-                if (t < nwords) {
-#pragma unroll
-                    for (uint32_t j = 0; j < 16; j++) {
-                        const uint32_t i = t * 16 + j;
-                        const uint32_t c = i < nbytes ? s_bytes[i] : 0u;
-                        const bool ok = c == 'A' || c == 'C' || c == 'G' || c == 'T';
-                        uint32_t b = (c >> 1) & 3u;  // A, C, T, G -> 0, 1, 2, 3
-                        b ^= b >> 1;                 // -> A 0, C 1, G 2, T 3
-                        pk = (pk << 2) | (ok ? b : 0u);
-                        inv = (inv << 1) | (ok ? 0u : 1u);
-                    }
-                }
-                s_pk[t] = pk;
-                s_inv[t] = (uint16_t)inv;
-            }
+            pack_bases(s_bytes, nbytes, s_pk, s_inv);
             __syncthreads();
         }
         // one window per thread and iteration; every lane of a warp runs the same
@@ -85,25 +66,9 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
             bool term = false;
             if (p < rn) {
                 if (dna) {
-                    const uint32_t w = p >> 4, o = p & 15u;
-                    // bases p .. p + k - 1: the top 2k bits of words w, w+1, w+2 shifted by 2o
-                    const uint64_t A = ((uint64_t)s_pk[w] << 32) | s_pk[w + 1];
-                    const uint64_t hi = o ? (A << (2 * o)) | (s_pk[w + 2] >> (32 - 2 * o)) : A;
-                    const uint64_t fwd = hi >> (64 - 2 * k);
-                    const uint64_t X = ((uint64_t)s_inv[w] << 32) | ((uint64_t)s_inv[w + 1] << 16) | s_inv[w + 2];
-                    term = ((X << (16 + o)) >> (64 - k)) == 0;
-                    if (a.kind == KIND_DNA_CANONICAL) {
-                        // reverse complement: complement, reverse the 2-bit groups
-                        uint64_t x = __brevll(~(fwd << (64 - 2 * k)));
-                        x = ((x >> 1) & 0x5555555555555555ULL) | ((x & 0x5555555555555555ULL) << 1);
-                        const uint64_t rc = x & mask;
-                        code = rc < fwd ? rc : fwd;
-                    } else {
-                        code = fwd;
-                    }
+                    term = packed_kmer(s_pk, s_inv, p, k, a.kind == KIND_DNA_CANONICAL, mask, &code);
                 } else {
-                    // q bytes little-endian
-                    for (uint32_t j = 0; j < k; j++) code |= (uint64_t)s_bytes[p + j] << (8 * j);
+                    code = bytes_qgram(s_bytes, p, k);
                     term = true;
                 }
             }
