@@ -224,7 +224,7 @@ def aggregate_over_ranks(seconds, units, dist=None, device="cpu"):
 
 
 # -------------------------------------------------------------------- serve
-def run_serve(dix, wl, rates, seconds, verify_oracle=None):
+def run_serve(dix, wl, rates, seconds, verify_oracle=None, inflight=3, wave_max=4096):
     """Poisson arrivals (cfg5 recipe on the given index) submitted at their
     arrival times from one thread, results polled from another; p50/p99 are the
     library's submit-to-visible latencies.  Optionally checks a seeded 1% sample
@@ -236,7 +236,7 @@ def run_serve(dix, wl, rates, seconds, verify_oracle=None):
         n = max(50, int(rate * seconds))
         qb, qo, thr, src, t_arr = synth.config5_queries(wl, n_q=n, rate=rate)
         ql = [bytes(qb[int(qo[i]):int(qo[i + 1])]) for i in range(n)]
-        srv = cobs.Server(dix, max_inflight_waves=3, max_wave_queries=4096)
+        srv = cobs.Server(dix, max_inflight_waves=inflight, max_wave_queries=wave_max)
         tickets = [None] * n
         results = [None] * n
         done_evt = threading.Event()
@@ -274,7 +274,9 @@ def run_serve(dix, wl, rates, seconds, verify_oracle=None):
         terms = sum(int(r[0]) for r in results if r is not None)
         rec = {"rate_qps": rate, "queries": n, "completed": int(stats["completed"]), "waves": int(stats["waves"]),
                "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "qps": stats["qps"],
-               "kmers_per_s": terms / stats["seconds"] if stats["seconds"] else None}
+               "kmers_per_s": terms / stats["seconds"] if stats["seconds"] else None,
+               "mean_wave_queries": stats["mean_wave_queries"], "mean_wave_ms": stats["mean_wave_ms"],
+               "max_wave_ms": stats["max_wave_ms"], "inflight_waves": inflight}
         if verify_oracle is not None:
             # a seeded 1% sample of the requests, each an independent single-threaded
             # oracle query (run side by side on the host cores)
@@ -470,7 +472,8 @@ def run_gpu(args):
     if args.serve_rates and args.config == "cfg2":
         del eng
         rates = [float(r) for r in args.serve_rates.split(",") if r]
-        out["serve"] = run_serve(dix, wl, rates, args.serve_seconds, verify_oracle=oracle_ix)
+        out["serve"] = run_serve(dix, wl, rates, args.serve_seconds, verify_oracle=oracle_ix,
+                                 inflight=args.serve_inflight, wave_max=args.serve_wave_max)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
@@ -498,6 +501,8 @@ def main():
     ap.add_argument("--serve-rates", default="1000,10000,50000",
                     help="Poisson arrival rates (queries/s) of the serving run on the cfg2 index; '' to skip")
     ap.add_argument("--serve-seconds", type=float, default=1.5)
+    ap.add_argument("--serve-inflight", type=int, default=3, help="waves on the device at once")
+    ap.add_argument("--serve-wave-max", type=int, default=4096, help="queries per wave at most")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -238,7 +238,9 @@ typedef struct cobs_serve_cfg {
 
 typedef struct cobs_serve_stats {
     uint64_t completed, waves, rejected;
-    double p50_ms, p99_ms, max_ms, qps, seconds;
+    double p50_ms, p99_ms, max_ms, qps, seconds;  /* latency: submit to result visible to poll */
+    double mean_wave_queries;                     /* queries per wave */
+    double mean_wave_ms, max_wave_ms;             /* wave launch to its results collected */
 } cobs_serve_stats;
 
 /* Start a serve loop on a device index (one scheduler thread; waves overlap on the

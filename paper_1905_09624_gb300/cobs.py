@@ -77,7 +77,8 @@ class cobs_serve_cfg(ctypes.Structure):
 class cobs_serve_stats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_uint64), ("waves", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("qps", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("qps", ctypes.c_double), ("seconds", ctypes.c_double), ("mean_wave_queries", ctypes.c_double),
+                ("mean_wave_ms", ctypes.c_double), ("max_wave_ms", ctypes.c_double)]
 
 
 _PROTOS = {

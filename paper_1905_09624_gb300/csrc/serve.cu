@@ -74,6 +74,8 @@ struct cobs_server {
     std::vector<std::unique_ptr<Slot>> slots;
     std::vector<double> lat_ms;
     uint64_t completed = 0, waves = 0, rejected = 0;
+    double wave_ms_sum = 0, wave_ms_max = 0;
+    uint64_t wave_queries = 0;
     double t_first = -1, t_last = 0;
     cobs_status fatal = COBS_OK;
 };
@@ -147,6 +149,10 @@ void collect_wave(cobs_server *S, Slot &sl, std::unique_lock<std::mutex> &lk) {
         S->completed++;
     }
     S->t_last = t;
+    const double wave_ms = (t - sl.t_launch) * 1e3;
+    S->wave_ms_sum += wave_ms;
+    S->wave_ms_max = std::max(S->wave_ms_max, wave_ms);
+    S->wave_queries += sl.reqs.size();
     if (res) cobs_result_free(res);
     S->budget_used -= sl.cost;
     sl.cost = 0;
@@ -330,6 +336,10 @@ extern "C" cobs_status cobs_serve_stop(cobs_server *S, cobs_serve_stats *out) {
         }
         out->seconds = S->t_first >= 0 ? S->t_last - S->t_first : 0.0;
         out->qps = out->seconds > 0 ? S->completed / out->seconds : 0.0;
+        const double nw = (double)(S->waves ? S->waves : 1);
+        out->mean_wave_queries = (double)S->wave_queries / nw;
+        out->mean_wave_ms = S->wave_ms_sum / nw;
+        out->max_wave_ms = S->wave_ms_max;
     }
     for (auto &sp : S->slots) {
         Slot &sl = *sp;
