@@ -179,7 +179,11 @@ typedef struct cobs_engine_cfg {
                                  0 = default (3), 1 = none, 2 = row indices evict-first,
                                  3 = row indices evict-first and index rows evict-last,
                                  4 = index rows evict-last */
-    uint32_t _pad;
+    uint32_t split;           /* long-query split of the batched form (single-hash indexes):
+                                 0 = auto (batches too small to give every resident warp
+                                 several tiles split queries of more than 4080 windows
+                                 into parts of 4080 terms, summed before the threshold),
+                                 1 = never, 2 = always */
 } cobs_engine_cfg;
 
 cobs_status cobs_engine_create(cobs_device_index *dix, const cobs_engine_cfg *cfg, void *stream,
@@ -215,7 +219,8 @@ cobs_status cobs_engine_download(cobs_engine *eng, cobs_result **out);
 typedef struct cobs_query_stats {
     double ms_terms, ms_gather, ms_hits, ms_total;
     uint64_t row_bytes, terms, n_tiles, gather_launches, launches;
-    uint32_t slice_bytes, ctas_per_sm, l2_hints, _pad;
+    uint32_t slice_bytes, ctas_per_sm, l2_hints;
+    uint32_t split_queries;   /* queries of the last batch that ran as split parts */
 } cobs_query_stats;
 cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out);
 

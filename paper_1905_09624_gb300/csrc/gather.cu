@@ -173,6 +173,21 @@ __device__ __forceinline__ void emit_hits(const GatherArgs &a, const DevBlock &b
     }
 }
 
+// A split item's counts for the lane's 128 documents (each below 2^16).
+template <int L>
+__device__ __forceinline__ void write_partials(const GatherArgs &a, const DevBlock &blk, uint32_t col,
+                                               uint32_t slot, const uint32_t (&lv)[4][L]) {
+    uint16_t *dst = a.partials + (uint64_t)slot * a.n_docs + blk.doc_begin;
+    const uint32_t doc0 = col * 8u;
+#pragma unroll
+    for (int w = 0; w < 4; w++) {
+        for (uint32_t bit = 0; bit < 32u; bit++) {
+            const uint32_t j = doc0 + 32u * w + bit;
+            if (j < blk.n_docs) dst[j] = (uint16_t)count_of<L>(lv[w], bit);
+        }
+    }
+}
+
 // One warp-tile of the register kernel: QPW queries x one row slice of one block.
 template <int LPQ, int G, int L>
 __device__ __forceinline__ void tile_body(const GatherArgs &a, const DevBlock &blk, uint32_t block_idx,
@@ -211,7 +226,7 @@ __global__ void __launch_bounds__(GATHER_THREADS) k_gather_batched(GatherArgs a)
         const DevBlock blk = a.blocks[sd.block];
         const uint32_t qi = g * QPW + qslot;
         const bool valid = qi < a.n_queries;
-        const uint32_t q = valid ? a.order[qi] : 0u;
+        const uint32_t q = valid ? a.items[qi].x : 0u;  // items of this kernel are whole queries
         const uint32_t ell = valid ? a.ell[q] : 0u;
         const uint32_t col = sd.byte_off + c * 16u;
         const bool active = valid && col < blk.rowbytes;
@@ -414,13 +429,15 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_gather_pipe(GatherArgs a) {
         const DevBlock blk = a.blocks[sd.block];
         const uint32_t qi = g0 * QPW + qslot;
         const bool valid = qi < a.n_queries;
-        const uint32_t q = valid ? a.order[qi] : 0u;
+        const uint4 it = valid ? a.items[qi] : make_uint4(0u, 0u, 0u, ITEM_WHOLE);
+        const uint32_t q = it.x;
         const uint32_t ell = valid ? a.ell[q] : 0u;
+        const uint32_t tend = ell < it.z ? ell : it.z;  // terms [it.y, tend) of the query
         const uint32_t col = sd.byte_off + c * 16u;
         const bool active = valid && col < blk.rowbytes;
-        const uint32_t n = active ? ell : 0u;
+        const uint32_t n = active && tend > it.y ? tend - it.y : 0u;
         const uint32_t ng = (n + PIPE_G - 1) / PIPE_G;
-        const uint32_t *ridx = a.rows_idx + (uint64_t)sd.block * a.tcap + a.term_base[q];
+        const uint32_t *ridx = a.rows_idx + (uint64_t)sd.block * a.tcap + a.term_base[q] + it.y;
         const uint8_t *colbase = a.rows + blk.row_offset + col;
         const uint32_t rowbytes = blk.rowbytes;
 
@@ -469,7 +486,11 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_gather_pipe(GatherArgs a) {
         }
         carry.flush(lv);
         cp_async_wait<0>();
-        if (n) emit_hits<L>(a, blk, col, q, ell, lv);
+        if (it.w == ITEM_WHOLE) {
+            if (n) emit_hits<L>(a, blk, col, q, ell, lv);
+        } else if (active) {
+            write_partials<L>(a, blk, col, it.w, lv);  // every part writes, zeros included
+        }
     }
 }
 
@@ -604,6 +625,52 @@ __global__ void k_plain_threshold(ThresholdArgs a) {
             }
         }
     }
+}
+
+// Split queries: score of a sorted position = sum of its items' partial counts;
+// the threshold and the warp-ballot compaction follow the plain form.
+__global__ void k_split_finish(SplitArgs a) {
+    for (uint32_t si = blockIdx.y; si < a.n_split; si += gridDim.y) {
+        const uint4 sp = a.split[si];
+        const uint32_t q = sp.x;
+        const uint32_t ell = a.ell[q];
+        if (ell == 0u) continue;
+        const uint32_t mn = (uint32_t)(((uint64_t)a.thr[q] * ell + 999u) / 1000u);
+        const uint32_t lane = threadIdx.x & 31u;
+        const uint32_t stride = gridDim.x * blockDim.x;
+        const uint32_t iters = (a.n_docs + stride - 1) / stride;
+        for (uint32_t it = 0; it < iters; it++) {
+            const uint32_t p = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+            uint32_t sc = 0;
+            if (p < a.n_docs)
+                for (uint32_t i = 0; i < sp.z; i++) sc += a.partials[(uint64_t)(sp.y + i) * a.n_docs + p];
+            const bool hit = p < a.n_docs && sc >= mn;
+            const uint32_t m = __ballot_sync(FULL, hit);
+            if (!m) continue;
+            unsigned long long base = 0;
+            const uint32_t leader = __ffs(m) - 1u;
+            if (lane == leader) {
+                base = atomicAdd(a.hit_count, (unsigned long long)__popc(m));
+                atomicAdd(&a.qcount[q], (uint32_t)__popc(m));
+            }
+            base = __shfl_sync(FULL, base, leader);
+            if (hit) {
+                const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
+                if (pos < a.hit_cap) {
+                    a.raw_q[pos] = q;
+                    a.raw_key[pos] = ((unsigned long long)(~sc) << 32) | a.perm[p];
+                }
+            }
+        }
+    }
+}
+
+void launch_split_finish(const SplitArgs &a, cudaStream_t s) {
+    if (a.n_split == 0 || a.n_docs == 0) return;
+    uint32_t bx = (a.n_docs + 255) / 256;
+    if (bx > 64) bx = 64;
+    const uint32_t by = a.n_split < 65535u ? a.n_split : 65535u;
+    k_split_finish<<<dim3(bx, by), 256, 0, s>>>(a);
 }
 
 void launch_plain_threshold(const ThresholdArgs &a, cudaStream_t s) {

@@ -537,6 +537,10 @@ extern "C" cobs_status cobs_engine_create(cobs_device_index *dix, const cobs_eng
         cobs_engine_free(eng);
         return set_error(COBS_ERR_ARG, "l2_hints must be 0..4");
     }
+    if (eng->cfg.split > 2) {
+        cobs_engine_free(eng);
+        return set_error(COBS_ERR_ARG, "split must be 0, 1 or 2");
+    }
     eng->l2_hints = eng->cfg.l2_hints ? eng->cfg.l2_hints : 3;
     eng->hit_cap = eng->cfg.max_hits ? eng->cfg.max_hits : (1ULL << 20);
     for (auto &e : eng->ev) cudaEventCreate(&e);
@@ -563,7 +567,7 @@ extern "C" void cobs_engine_free(cobs_engine *eng) {
 }
 
 // Plan a batch from the host offsets.
-static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n, BatchPlan &bp) {
+static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n, bool batched, BatchPlan &bp) {
     const cobs_params &P = eng->dix->params;
     const uint32_t k = P.q;
     const uint64_t limit = P.score_bits == 16 ? 0xFFFFULL : 0xFFFFFFFFULL;
@@ -571,7 +575,6 @@ static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n
     bp.npos.resize(n);
     bp.term_base.resize(n);
     bp.table_base.resize(n);
-    bp.order.resize(n);
     bp.tcap = 0;
     bp.total_slots = 0;
     bp.sum_npos = 0;
@@ -600,24 +603,66 @@ static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n
         bp.max_npos = std::max(bp.max_npos, np);
     }
     if (bp.tcap == 0) bp.tcap = TERM_ALIGN;
-    std::iota(bp.order.begin(), bp.order.end(), 0u);
-    std::stable_sort(bp.order.begin(), bp.order.end(),
-                     [&](uint32_t a, uint32_t b) { return bp.npos[a] > bp.npos[b]; });
+    std::vector<uint32_t> order(n);
+    std::iota(order.begin(), order.end(), 0u);
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return bp.npos[a] > bp.npos[b]; });
+    // Work items.  A batch too small to give every resident warp several tiles
+    // splits its long queries into items of SPLIT_TERMS terms (h == 1 only), so
+    // one long query no longer runs on a single warp per slice.
+    const uint64_t qpw = 32 / eng->lanes_per_query;
+    const uint64_t warps = (uint64_t)eng->n_sm * eng->ctas_per_sm * 2;
+    const bool small = (uint64_t)eng->n_slices * ((n + qpw - 1) / qpw) < 4 * warps;
+    bool split = batched && P.num_hashes == 1 && eng->cfg.split != 1 && (eng->cfg.split == 2 || small);
+    if (split) {  // partial counts (2 bytes per part and document) stay below 1 GiB
+        uint64_t parts = 0;
+        for (uint64_t q = 0; q < n; q++)
+            if (bp.npos[q] > SPLIT_TERMS) parts += (bp.npos[q] + SPLIT_TERMS - 1) / SPLIT_TERMS;
+        split = parts * eng->dix->n_docs * 2 <= (1ULL << 30);
+    }
+    bp.items.clear();
+    bp.split.clear();
+    bp.n_parts = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        const uint32_t q = order[i];
+        const uint64_t np = bp.npos[q];
+        if (split && np > SPLIT_TERMS) {
+            const uint32_t parts = (uint32_t)((np + SPLIT_TERMS - 1) / SPLIT_TERMS);
+            bp.split.push_back({q, (uint32_t)bp.n_parts, parts, 0u});
+            for (uint32_t p = 0; p < parts; p++)
+                bp.items.push_back({q, p * SPLIT_TERMS, (p + 1) * SPLIT_TERMS, (uint32_t)(bp.n_parts + p)});
+            bp.n_parts += parts;
+        } else {
+            bp.items.push_back({q, 0u, ITEM_WHOLE, ITEM_WHOLE});
+        }
+    }
+    // longest items first; counter width classes by the items' term bounds
+    auto bound = [&](const BatchPlan::Item &it) {
+        return std::min<uint64_t>(bp.npos[it.q], it.lim) - std::min<uint64_t>(bp.npos[it.q], it.t0);
+    };
+    std::stable_sort(bp.items.begin(), bp.items.end(),
+                     [&](const BatchPlan::Item &a, const BatchPlan::Item &b) { return bound(a) > bound(b); });
     bp.classes.clear();
-    for (uint32_t i = 0; i < n;) {
-        uint32_t L = counter_levels_for((uint32_t)bp.npos[bp.order[i]]);
+    const uint32_t ni = (uint32_t)bp.items.size();
+    for (uint32_t i = 0; i < ni;) {
+        uint32_t L = counter_levels_for((uint32_t)bound(bp.items[i]));
         uint32_t j = i;
-        while (j < n && counter_levels_for((uint32_t)bp.npos[bp.order[j]]) == L) j++;
+        while (j < ni && counter_levels_for((uint32_t)bound(bp.items[j])) == L) j++;
         bp.classes.push_back({i, j - i, L});
         i = j;
     }
     return COBS_OK;
 }
 
+// Plan upload: term_base[n] | table_base[n] (u64) | items | split queries (uint4).
+static uint64_t plan_bytes(const BatchPlan &bp) {
+    return bp.n * 16 + bp.items.size() * 16 + bp.split.size() * 16;
+}
+
 static cobs_status ensure_buffers(cobs_engine *eng, const BatchPlan &bp) {
     const uint64_t n = bp.n;
     const uint64_t nb = eng->dix->blocks.size(), h = eng->dix->params.num_hashes;
-    CU(eng->plan.ensure(n * 20 + 64));
+    CU(eng->plan.ensure(plan_bytes(bp) + 64));
+    CU(eng->partials.ensure(bp.n_parts * eng->dix->n_docs * 2));
     CU(eng->ell.ensure(n * 4));
     CU(eng->minsc.ensure(n * 4));
     CU(eng->qcount.ensure(n * 4 + 64 * 8));  // qcount, then the counters (one memset clears both)
@@ -634,7 +679,7 @@ static cobs_status ensure_buffers(cobs_engine *eng, const BatchPlan &bp) {
     CU(eng->out_ids.ensure(eng->hit_cap * 4));
     CU(eng->out_scores.ensure(eng->hit_cap * 4));
     CU(eng->scores.ensure(eng->dix->n_docs * 4));
-    CU(eng->pin_plan.ensure(n * 20 + 64));
+    CU(eng->pin_plan.ensure(plan_bytes(bp) + 64));
     CU(eng->pin_count.ensure(64));
     return COBS_OK;
 }
@@ -657,7 +702,8 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
     uint8_t *plan = eng->plan.as<uint8_t>();
     const uint64_t *term_base = (const uint64_t *)plan;
     const uint64_t *table_base = (const uint64_t *)(plan + n * 8);
-    const uint32_t *order = (const uint32_t *)(plan + n * 16);
+    const uint4 *items = (const uint4 *)(plan + n * 16);
+    const uint4 *split = items + bp.items.size();
     unsigned long long *ctr = counters_of(eng, n);
     eng->stat_launches = 0;
     eng->stat_gather_launches = 0;
@@ -665,7 +711,7 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
 
     if (timed) CU(cudaEventRecord(eng->ev[0], s));
     CU(cudaMemsetAsync(eng->qcount.p, 0, (uint8_t *)(ctr + 16) - eng->qcount.as<uint8_t>(), s));
-    CU(cudaMemcpyAsync(plan, eng->pin_plan.p, n * 20, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(plan, eng->pin_plan.p, plan_bytes(bp), cudaMemcpyHostToDevice, s));
 
     TermsArgs ta{};
     ta.bytes = d_bytes;
@@ -743,13 +789,13 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
             ga.term_base = term_base;
             ga.ell = eng->ell.as<uint32_t>();
             ga.thr = d_thr;
-            ga.order = order + cl.begin;
+            ga.items = items + cl.begin;
             ga.n_queries = cl.count;
             ga.h = P.num_hashes;
             ga.slices = eng->slices.as<SliceDesc>();
             ga.n_slices = eng->n_slices;
             ga.n_groups = (cl.count + qpw - 1) / qpw;
-            ga.work_counter = ctr + 1 + (c % 15);
+            ga.work_counter = ctr + 1 + (c % 14);  // ctr[15] is the big-segment count
             ga.hit_count = ctr;
             ga.qcount = eng->qcount.as<uint32_t>();
             ga.raw_q = eng->raw_q.as<uint32_t>();
@@ -758,11 +804,30 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
             // l2_hints: 1 none, 2 row indices evict-first, 3 + index rows evict-last, 4 rows evict-last only
             ga.l2_idx_policy = (eng->l2_hints == 2 || eng->l2_hints == 3) ? 1u : 0u;
             ga.l2_row_policy = (eng->l2_hints == 3 || eng->l2_hints == 4) ? 2u : 0u;
+            ga.partials = eng->partials.as<uint16_t>();
+            ga.n_docs = (uint32_t)dix->n_docs;
             if (ga.n_slices == 0 || ga.n_groups == 0) continue;
             launch_gather_batched_L(ga, eng->lanes_per_query, cl.L, grid, s);
             eng->stat_launches += 1;
             eng->stat_gather_launches += 1;
             eng->stat_tiles += (uint64_t)ga.n_slices * ga.n_groups;
+        }
+        if (!bp.split.empty()) {
+            SplitArgs sa{};
+            sa.split = split;
+            sa.n_split = (uint32_t)bp.split.size();
+            sa.partials = eng->partials.as<uint16_t>();
+            sa.n_docs = (uint32_t)dix->n_docs;
+            sa.perm = dix->dperm.as<uint32_t>();
+            sa.ell = eng->ell.as<uint32_t>();
+            sa.thr = d_thr;
+            sa.hit_count = ctr;
+            sa.qcount = eng->qcount.as<uint32_t>();
+            sa.raw_q = eng->raw_q.as<uint32_t>();
+            sa.raw_key = eng->raw_key.as<unsigned long long>();
+            sa.hit_cap = eng->hit_cap;
+            launch_split_finish(sa, s);
+            eng->stat_launches += 1;
         }
         CU(cudaGetLastError());
         if (timed) CU(cudaEventRecord(eng->ev[2], s));
@@ -798,7 +863,8 @@ static void fill_pinned_plan(cobs_engine *eng) {
     uint8_t *p = eng->pin_plan.as<uint8_t>();
     memcpy(p, bp.term_base.data(), bp.n * 8);
     memcpy(p + bp.n * 8, bp.table_base.data(), bp.n * 8);
-    memcpy(p + bp.n * 16, bp.order.data(), bp.n * 4);
+    if (!bp.items.empty()) memcpy(p + bp.n * 16, bp.items.data(), bp.items.size() * 16);
+    if (!bp.split.empty()) memcpy(p + bp.n * 16 + bp.items.size() * 16, bp.split.data(), bp.split.size() * 16);
 }
 
 static std::vector<uint64_t> graph_signature(cobs_engine *eng, const uint8_t *d_bytes, const uint64_t *d_off,
@@ -813,7 +879,9 @@ static std::vector<uint64_t> graph_signature(cobs_engine *eng, const uint8_t *d_
                                  (uint64_t)eng->hitoff.p, (uint64_t)eng->raw_key.p, (uint64_t)eng->keys.p,
                                  (uint64_t)eng->biglist.p,
                                  (uint64_t)eng->tmp.p, (uint64_t)eng->out_ids.p, (uint64_t)eng->out_scores.p,
-                                 (uint64_t)eng->pin_count.p, (uint64_t)eng->slices.p, eng->n_slices};
+                                 (uint64_t)eng->pin_count.p, (uint64_t)eng->slices.p, eng->n_slices,
+                                 (uint64_t)bp.items.size(), (uint64_t)bp.split.size(), bp.n_parts,
+                                 (uint64_t)eng->partials.p};
     for (const auto &c : bp.classes) {
         sig.push_back(c.begin);
         sig.push_back(c.count);
@@ -831,7 +899,7 @@ cobs_status engine_query(cobs_engine *eng, const uint8_t *d_bytes, const uint64_
         return set_error(COBS_ERR_ARG, "flags must be COBS_PLAIN, COBS_BATCHED or COBS_GRAPH");
     if (n >= 0x7FFFFFFFULL) return set_error(COBS_ERR_ARG, "too many queries in one batch");
     CU(cudaSetDevice(eng->dix->device));
-    TRY(make_plan(eng, h_off, n, eng->bp));
+    TRY(make_plan(eng, h_off, n, flags != COBS_PLAIN, eng->bp));
     TRY(ensure_buffers(eng, eng->bp));
     eng->last_bytes = d_bytes;
     eng->last_off = d_off;
@@ -1063,6 +1131,7 @@ extern "C" cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out
     out->slice_bytes = eng->lanes_per_query * 16;
     out->ctas_per_sm = eng->ctas_per_sm;
     out->l2_hints = eng->l2_hints;
+    out->split_queries = (uint32_t)eng->bp.split.size();
     return COBS_OK;
 }
 

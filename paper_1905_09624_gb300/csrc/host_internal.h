@@ -70,11 +70,16 @@ struct BatchPlan {
     uint64_t n = 0;
     std::vector<uint64_t> npos;
     std::vector<uint64_t> term_base, table_base;
-    std::vector<uint32_t> order;
     struct Class {
-        uint32_t begin, count, L;
+        uint32_t begin, count, L;  // a run of items with the same counter width
     };
     std::vector<Class> classes;
+    struct Item {
+        uint32_t q, t0, lim, slot;  // same layout as the device's uint4 items
+    };
+    std::vector<Item> items;        // work items of the batched kernel
+    std::vector<Item> split;        // split queries: (query, first slot, slots, 0)
+    uint64_t n_parts = 0;           // partial slots
     uint64_t tcap = 0, total_slots = 0, sum_npos = 0, max_npos = 0;
     uint32_t smem_slots = 16;  // largest distinct set of the batch kept in shared memory
 };
@@ -115,7 +120,8 @@ struct cobs_engine {
 
     // per batch
     cobs::DevBuf qbytes, qoff, thr;          // staging of host queries
-    cobs::DevBuf plan;                        // term_base | table_base | order
+    cobs::DevBuf plan;                        // term_base | table_base | items | split
+    cobs::DevBuf partials;                    // split items: counts per (slot, document)
     cobs::DevBuf ell, minsc, qcount, qcursor, hitoff, biglist;
     cobs::DevBuf counters;                    // [0] hit count, [1..] work counters
     cobs::DevBuf rows_idx, tables, codes;

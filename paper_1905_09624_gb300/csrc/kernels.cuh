@@ -46,8 +46,11 @@ struct GatherArgs {
     const uint64_t *term_base;
     const uint32_t *ell;
     const uint16_t *thr;
-    const uint32_t *order;         // queries in processing order (longest first)
-    uint32_t n_queries;
+    // Work items in processing order (longest first): x = query, y = first term,
+    // z = term limit (the item covers terms [y, min(l, z))), w = partial slot, or
+    // ITEM_WHOLE when the item is the whole query (threshold in the epilogue).
+    const uint4 *items;
+    uint32_t n_queries;            // items in this launch
     uint32_t h;
     const SliceDesc *slices;
     uint32_t n_slices;
@@ -60,7 +63,30 @@ struct GatherArgs {
     uint64_t hit_cap;
     uint32_t l2_idx_policy;        // L2 eviction priority of row-index loads: 0 normal, 1 first, 2 last
     uint32_t l2_row_policy;        // same for the gathered index rows
+    uint16_t *partials;            // split items: counts per (partial slot, sorted position)
+    uint32_t n_docs;
 };
+constexpr uint32_t ITEM_WHOLE = 0xFFFFFFFFu;
+// Long queries of small batches are split into items of SPLIT_TERMS terms (a
+// multiple of TERM_ALIGN below 2^12, so a part counts in 12 bit-sliced levels).
+constexpr uint32_t SPLIT_TERMS = 4080;
+
+// Split queries: sum the partial counts of their items, threshold, emit hits.
+struct SplitArgs {
+    const uint4 *split;            // x = query, y = first partial slot, z = slots
+    uint32_t n_split;
+    const uint16_t *partials;
+    uint32_t n_docs;
+    const uint32_t *perm;
+    const uint32_t *ell;
+    const uint16_t *thr;
+    unsigned long long *hit_count;
+    uint32_t *qcount;
+    uint32_t *raw_q;
+    unsigned long long *raw_key;
+    uint64_t hit_cap;
+};
+void launch_split_finish(const SplitArgs &a, cudaStream_t s);
 // lanes_per_query in {2, 4, 8}: slice = 16 * lanes_per_query bytes.  L = counter
 // levels (8, 12, 16 or 24): every query of the launch has fewer than 2^L terms.
 void launch_gather_batched_L(const GatherArgs &a, uint32_t lanes_per_query, uint32_t L, uint32_t grid,
