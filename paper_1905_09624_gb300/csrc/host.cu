@@ -639,8 +639,9 @@ static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n
     auto bound = [&](const BatchPlan::Item &it) {
         return std::min<uint64_t>(bp.npos[it.q], it.lim) - std::min<uint64_t>(bp.npos[it.q], it.t0);
     };
-    std::stable_sort(bp.items.begin(), bp.items.end(),
-                     [&](const BatchPlan::Item &a, const BatchPlan::Item &b) { return bound(a) > bound(b); });
+    if (!bp.split.empty())  // without parts the items already follow the query order
+        std::stable_sort(bp.items.begin(), bp.items.end(),
+                         [&](const BatchPlan::Item &a, const BatchPlan::Item &b) { return bound(a) > bound(b); });
     bp.classes.clear();
     const uint32_t ni = (uint32_t)bp.items.size();
     for (uint32_t i = 0; i < ni;) {

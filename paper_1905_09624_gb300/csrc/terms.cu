@@ -3,31 +3,41 @@
 // open-addressing set, then for every distinct term and every block b and hash
 // i < h its row XXH64(term, i) mod w_b (Sec. 2.2), written as a u32 row index.
 //
-// The query is processed in rounds of TERMS_ROUND windows.  Each round stages
-// its bytes in shared memory (coalesced loads) and, for DNA, packs them into a
-// 2-bit base stream and a mask of non-ACGT bytes, 16 bases per word.  Every
+// The query is processed in rounds of TERMS_ROUND windows.  For DNA each round
+// packs its bytes straight from global memory into a 2-bit base stream and a
+// mask of non-ACGT bytes, 16 bases per word (every thread packs 4 bytes, four
+// lanes merge a word); byte q-grams stage the bytes in shared memory.  Every
 // thread then takes one window at a time: its k bases are a funnel shift of
 // three packed words, its validity a shift of the mask, its reverse complement a
 // bit reversal of the complemented code with the bits of each base swapped back.
 // The window is hashed, inserted into the set and appended to the distinct list
-// when it is new (warp-aggregated).  The list holds hash 0 when h == 1 (all the
-// row pass needs), else the code.  A final pass writes the rows in row-bucket
-// order.
+// when it is new (warp-aggregated).  A final pass writes the rows in row-bucket
+// order.  With one hash and at most two blocks the rows of a new term are
+// computed at insertion: the list holds them (block 1 in the high word) and the
+// bucket histogram is counted on the way, so the final pass only scatters.
+// Otherwise the list holds hash 0 when h == 1, else the code, and the final pass
+// recomputes the rows.
 #include "kernels.cuh"
 
 namespace cobs {
 
 constexpr uint32_t TERMS_ROUND = TERMS_THREADS * TERMS_SEG;  // windows per round
 constexpr uint32_t TERMS_STAGE_BYTES = TERMS_ROUND + 32;      // + k - 1 <= 31 bytes of overlap
+// packed words of a round: data words + 2 read past the last window, rounded up
+// so the packing loop runs whole warps (4 bytes per lane, 8 words per warp)
+constexpr uint32_t TERMS_PK_WORDS = (((TERMS_STAGE_BYTES + 15) / 16 + 2) * 4 + 31) / 32 * 8;
 
 __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     extern __shared__ unsigned long long s_table[];
     __shared__ __align__(16) uint8_t s_bytes[TERMS_STAGE_BYTES];
     __shared__ unsigned long long s_list[TERMS_ROUND];  // distinct list of an on-chip set
-    __shared__ uint32_t s_pk[TERMS_STAGE_BYTES / 16 + 3];   // 2-bit bases, 16 per word
-    __shared__ uint16_t s_inv[TERMS_STAGE_BYTES / 16 + 3];  // non-ACGT bytes, 16 per word
+    __shared__ uint32_t s_pk[TERMS_PK_WORDS];   // 2-bit bases, 16 per word
+    __shared__ uint16_t s_inv[TERMS_PK_WORDS];  // non-ACGT bytes, 16 per word
     __shared__ uint32_t s_ell;
     __shared__ uint32_t s_has_empty;
+    constexpr uint32_t BP = TERMS_BLOCKS_PER_PASS;
+    __shared__ uint32_t s_hist[BP * TERMS_BUCKETS];
+    __shared__ uint32_t s_shift[BP];
 
     const uint32_t q = a.q0 + blockIdx.x;
     const uint64_t off0 = a.offsets[q];
@@ -44,6 +54,21 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     for (uint32_t i = threadIdx.x; i < cap; i += blockDim.x) table[i] = EMPTY_KEY;
     if (threadIdx.x == 0) { s_ell = 0; s_has_empty = 0; }
 
+    // rows at insertion (one hash, at most two blocks): block moduli in shared memory
+    const bool rows_in_list = a.h == 1 && a.n_blocks <= 2;
+    const uint32_t nb_fast = rows_in_list ? a.n_blocks : 0u;
+    __shared__ uint64_t s_fm[2];
+    __shared__ uint32_t s_fw[2];
+    if (threadIdx.x < nb_fast) {
+        const DevBlock blk = a.blocks[threadIdx.x];
+        s_fm[threadIdx.x] = blk.barrett_m;
+        s_fw[threadIdx.x] = blk.w;
+        const int lg = 32 - __clz(blk.w > 1 ? blk.w - 1 : 0);  // bits of the largest row
+        s_shift[threadIdx.x] = lg > (int)TERMS_BUCKET_BITS ? (uint32_t)(lg - TERMS_BUCKET_BITS) : 0u;
+    }
+    if (rows_in_list)
+        for (uint32_t i = threadIdx.x; i < 2 * TERMS_BUCKETS; i += blockDim.x) s_hist[i] = 0;
+
     const uint8_t *src = a.bytes + off0;
     const uint64_t mask = kmer_mask(k);
     const uint32_t lane = threadIdx.x & 31u;
@@ -52,13 +77,38 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     for (uint64_t r0 = 0; r0 < npos; r0 += TERMS_ROUND) {
         const uint32_t rn = (uint32_t)(npos - r0 < TERMS_ROUND ? npos - r0 : TERMS_ROUND);
         const uint32_t nbytes = rn + k - 1;
-        __syncthreads();  // previous round finished with s_bytes (and the table init)
-        for (uint32_t i = threadIdx.x; i < nbytes; i += blockDim.x) s_bytes[i] = src[r0 + i];
-        __syncthreads();
+        __syncthreads();  // previous round finished with the staged bases (and the table init)
         if (dna) {
-            pack_bases(s_bytes, nbytes, s_pk, s_inv);
-            __syncthreads();
+            // 4 bytes per lane -> 8 bits of bases and 4 mask bits; lanes 4j..4j+3 form word j
+            const uint32_t nquads = (((nbytes + 15) / 16 + 2) * 4 + 31) & ~31u;
+            for (uint32_t t = threadIdx.x; t < nquads; t += blockDim.x) {
+                uint32_t pk = 0, inv = 0;
+#pragma unroll
+                for (uint32_t j = 0; j < 4; j++) {
+                    const uint32_t i = 4 * t + j;
+                    const uint32_t c = i < nbytes ? src[r0 + i] : 0u;
+                    const bool ok = c == 'A' || c == 'C' || c == 'G' || c == 'T';
+                    uint32_t b = (c >> 1) & 3u;  // A, C, T, G -> 0, 1, 2, 3
+                    b ^= b >> 1;                 // -> A 0, C 1, G 2, T 3
+                    pk = (pk << 2) | (ok ? b : 0u);
+                    inv = (inv << 1) | (ok ? 0u : 1u);
+                }
+                const uint32_t sub = 3u - (t & 3u);  // first quad of a word is most significant
+                pk <<= 8 * sub;
+                inv <<= 4 * sub;
+                pk |= __shfl_xor_sync(0xffffffffu, pk, 1);
+                inv |= __shfl_xor_sync(0xffffffffu, inv, 1);
+                pk |= __shfl_xor_sync(0xffffffffu, pk, 2);
+                inv |= __shfl_xor_sync(0xffffffffu, inv, 2);
+                if ((t & 3u) == 0u) {
+                    s_pk[t >> 2] = pk;
+                    s_inv[t >> 2] = (uint16_t)inv;
+                }
+            }
+        } else {
+            for (uint32_t i = threadIdx.x; i < nbytes; i += blockDim.x) s_bytes[i] = src[r0 + i];
         }
+        __syncthreads();
         // one window per thread and iteration; every lane of a warp runs the same
         // number of iterations, for the warp-level append
         for (uint32_t p = threadIdx.x; p < ((rn + 31u) & ~31u); p += blockDim.x) {
@@ -85,13 +135,58 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
                 const uint32_t leader = __ffs(m) - 1;
                 if (lane == leader) slot0 = atomicAdd(&s_ell, (uint32_t)__popc(m));
                 slot0 = __shfl_sync(0xffffffffu, slot0, leader);
-                if (fresh) list[slot0 + __popc(m & ((1u << lane) - 1u))] = a.h == 1 ? h0 : code;
+                if (fresh) {
+                    uint64_t entry = a.h == 1 ? h0 : code;
+                    if (rows_in_list) {
+                        const uint32_t rw0 = barrett_mod(h0, s_fm[0], s_fw[0]);
+                        atomicAdd(&s_hist[rw0 >> s_shift[0]], 1u);
+                        uint32_t rw1 = 0;
+                        if (nb_fast > 1) {
+                            rw1 = barrett_mod(h0, s_fm[1], s_fw[1]);
+                            atomicAdd(&s_hist[TERMS_BUCKETS + (rw1 >> s_shift[1])], 1u);
+                        }
+                        entry = ((uint64_t)rw1 << 32) | rw0;
+                    }
+                    list[slot0 + __popc(m & ((1u << lane) - 1u))] = entry;
+                }
             }
         }
     }
     __syncthreads();
     const uint32_t ell = s_ell;
     if (threadIdx.x == 0) a.ell[q] = ell;
+    const uint32_t warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    // exclusive scan of the 64 bucket counts of block j, by one warp
+    auto scan_hist = [&](uint32_t *hj) {
+        uint32_t carry = 0;
+        for (uint32_t c0 = 0; c0 < TERMS_BUCKETS; c0 += 32) {
+            const uint32_t v = hj[c0 + lane];
+            uint32_t x = v;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+                if ((int)lane >= d) x += y;
+            }
+            hj[c0 + lane] = carry + x - v;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+    };
+    if (rows_in_list) {
+        for (uint32_t j = warp; j < nb_fast; j += n_warps) scan_hist(s_hist + j * TERMS_BUCKETS);
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < ell; t += blockDim.x) {
+            const uint64_t e = list[t];
+#pragma unroll
+            for (uint32_t j = 0; j < 2; j++) {
+                if (j < nb_fast) {
+                    const uint32_t r = (uint32_t)(e >> (32 * j));
+                    const uint32_t pos = atomicAdd(&s_hist[j * TERMS_BUCKETS + (r >> s_shift[j])], 1u);
+                    a.rows_idx[(uint64_t)j * a.tcap + base + pos] = r;
+                }
+            }
+        }
+        return;
+    }
     // every distinct term once, spread over the threads: f(code, hash 0); the code
     // is only meaningful (and only used) when h > 1
     auto each_distinct = [&](auto &&f) {
@@ -107,10 +202,6 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     // a slice together, so the rows in use at any moment form a narrow band.
     // Blocks are handled TERMS_BLOCKS_PER_PASS at a time, so every term is hashed
     // once per pass whatever the number of blocks.
-    constexpr uint32_t BP = TERMS_BLOCKS_PER_PASS;
-    __shared__ uint32_t s_hist[BP * TERMS_BUCKETS];
-    __shared__ uint32_t s_shift[BP];
-    const uint32_t warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
     for (uint32_t b0 = 0; b0 < a.n_blocks; b0 += BP) {
         const uint32_t nbp = a.n_blocks - b0 < BP ? a.n_blocks - b0 : BP;
         for (uint32_t i = threadIdx.x; i < nbp * TERMS_BUCKETS; i += blockDim.x) s_hist[i] = 0;
@@ -131,21 +222,7 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
             }
         });
         __syncthreads();
-        for (uint32_t j = warp; j < nbp; j += n_warps) {  // exclusive scan per block, one warp each
-            uint32_t *hj = s_hist + j * TERMS_BUCKETS;
-            uint32_t carry = 0;
-            for (uint32_t c0 = 0; c0 < TERMS_BUCKETS; c0 += 32) {
-                const uint32_t v = hj[c0 + lane];
-                uint32_t x = v;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-                    if ((int)lane >= d) x += y;
-                }
-                hj[c0 + lane] = carry + x - v;
-                carry += __shfl_sync(0xffffffffu, x, 31);
-            }
-        }
+        for (uint32_t j = warp; j < nbp; j += n_warps) scan_hist(s_hist + j * TERMS_BUCKETS);
         __syncthreads();
         each_distinct([&](uint64_t code, uint64_t h0) {
             uint32_t pos[BP];
