@@ -393,7 +393,7 @@ def run_gpu(args):
     T, terms_all = aggregate_over_ranks(sum(step_ms) / 1e3, terms_total, dist, device="cuda")
     value = terms_all / T
 
-    phases = {k: st[k] for k in ("ms_terms", "ms_gather", "ms_hits", "ms_total")}
+    phases = {k: st[k] for k in ("ms_terms", "ms_gather", "ms_hits", "ms_total", "ms_host")}
     # ---- results of the timed form, kept for the plain comparison
     batched_res = eng.download_arrays()
 

@@ -221,6 +221,7 @@ typedef struct cobs_query_stats {
     uint64_t row_bytes, terms, n_tiles, gather_launches, launches;
     uint32_t slice_bytes, ctas_per_sm, l2_hints;
     uint32_t split_queries;   /* queries of the last batch that ran as split parts */
+    double ms_host;           /* host time of the last query call: planning and enqueueing */
 } cobs_query_stats;
 cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out);
 

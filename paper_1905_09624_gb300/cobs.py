@@ -65,7 +65,7 @@ class cobs_query_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("row_bytes", ctypes.c_uint64), ("terms", ctypes.c_uint64),
                 ("n_tiles", ctypes.c_uint64), ("gather_launches", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("slice_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("l2_hints", ctypes.c_uint32),
-                ("split_queries", ctypes.c_uint32)]
+                ("split_queries", ctypes.c_uint32), ("ms_host", ctypes.c_double)]
 
 
 class cobs_serve_cfg(ctypes.Structure):

@@ -2,6 +2,7 @@
 // build (Sec. 2.3 "Classic and Compact"), index transfer and files, the query
 // engine with its plain, batched and graph forms, and result assembly.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -605,7 +606,8 @@ static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n
     if (bp.tcap == 0) bp.tcap = TERM_ALIGN;
     std::vector<uint32_t> order(n);
     std::iota(order.begin(), order.end(), 0u);
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return bp.npos[a] > bp.npos[b]; });
+    auto longer = [&](uint32_t a, uint32_t b) { return bp.npos[a] > bp.npos[b]; };
+    if (!std::is_sorted(order.begin(), order.end(), longer)) std::stable_sort(order.begin(), order.end(), longer);
     // Work items.  A batch too small to give every resident warp several tiles
     // splits its long queries into items of SPLIT_TERMS terms (h == 1 only), so
     // one long query no longer runs on a single warp per slice.
@@ -899,6 +901,7 @@ cobs_status engine_query(cobs_engine *eng, const uint8_t *d_bytes, const uint64_
     if (flags != COBS_PLAIN && flags != COBS_BATCHED && flags != COBS_GRAPH && flags != (COBS_GRAPH | COBS_BATCHED))
         return set_error(COBS_ERR_ARG, "flags must be COBS_PLAIN, COBS_BATCHED or COBS_GRAPH");
     if (n >= 0x7FFFFFFFULL) return set_error(COBS_ERR_ARG, "too many queries in one batch");
+    const auto t_host = std::chrono::steady_clock::now();
     CU(cudaSetDevice(eng->dix->device));
     TRY(make_plan(eng, h_off, n, flags != COBS_PLAIN, eng->bp));
     TRY(ensure_buffers(eng, eng->bp));
@@ -951,6 +954,7 @@ cobs_status engine_query(cobs_engine *eng, const uint8_t *d_bytes, const uint64_
     }
     CU(cudaEventRecord(eng->ev_done, eng->stream));
     eng->pending = true;
+    eng->stat_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host).count();
     return COBS_OK;
 }
 
@@ -1133,6 +1137,7 @@ extern "C" cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out
     out->ctas_per_sm = eng->ctas_per_sm;
     out->l2_hints = eng->l2_hints;
     out->split_queries = (uint32_t)eng->bp.split.size();
+    out->ms_host = eng->stat_host_ms;
     return COBS_OK;
 }
 

@@ -149,6 +149,7 @@ struct cobs_engine {
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t ev_done = nullptr;
     uint64_t stat_launches = 0, stat_gather_launches = 0, stat_tiles = 0;
+    double stat_host_ms = 0;
     uint64_t hit_off_cache = 0;
 };
 
