@@ -428,6 +428,38 @@ def run_gpu(args):
         plain = {"value": pr[0]["terms"] / pt, "unit": UNIT, "ms": pt * 1e3,
                  "row_gbs_logical": pr[0]["row_bytes"] / pt / 1e9,
                  "launches": pr[0]["launches"], "results_identical_to_batched": bool(same)}
+    # ---- the same batch on a streamed copy of the index: rows in pinned host
+    # memory, copied block by block into a ring of device slots every step
+    streamed = None
+    if not args.skip_streamed:
+        sdix = cobs.DeviceIndex.load_streamed(dix.download(), device=local)
+        seng = cobs.Engine(sdix, stream=sh, slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm,
+                           stage_bytes=args.stage_bytes)
+        for _ in range(3):
+            flush_l2()
+            seng.query_device(d_q, d_off, wl.q_off, d_thr, form)
+            seng.stats()
+        s_ms, s_terms = [], 0
+        for i in range(args.streamed_steps):
+            flush_l2()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            seng.query_device(d_q, d_off, wl.q_off, d_thr, form)
+            e1.record(stream)
+            sst = seng.stats()
+            s_ms.append(e0.elapsed_time(e1))
+            s_terms += sst["terms"]
+        same = all(np.array_equal(a, b) for a, b in zip(seng.download_arrays(), batched_res))
+        slot = max(b["w"] * b["rowbytes"] for b in info["blocks"])
+        slot = (slot + 255) // 256 * 256
+        n_slots = min(len(info["blocks"]), args.stage_bytes // slot if args.stage_bytes else 2)
+        sm = float(np.mean(s_ms))
+        streamed = {"value": s_terms / args.streamed_steps / (sm / 1e3), "unit": UNIT, "ms_per_step": sm,
+                    "steps": args.streamed_steps, "h2d_index_bytes_per_step": sst["h2d_index_bytes"],
+                    "h2d_index_gbs": sst["h2d_index_bytes"] / (sm / 1e3) / 1e9, "stage_slots": n_slots,
+                    "stage_bytes": n_slots * slot, "index_bytes": info["rows_bytes"],
+                    "results_identical_to_resident": bool(same)}
+        del seng, sdix
     sampler.stop()
     clocks = sampler.summary(t_wall0, t_wall1)
 
@@ -459,7 +491,8 @@ def run_gpu(args):
                      "gbs_device": int(wl.doc_off[-1]) / (min(build_ms) / 1e3) / 1e9,
                      "gbs_with_h2d": int(wl.doc_off[-1]) / build_h2d_s / 1e9,
                      "index_bytes": info["rows_bytes"], "blocks": len(info["blocks"])},
-           "speedup_batched_over_plain": (value / plain["value"]) if plain else None}
+           "speedup_batched_over_plain": (value / plain["value"]) if plain else None,
+           "streamed": streamed}
     if plain:
         out["plain"]["frac_of_hbm_peak"] = plain["row_gbs_logical"] / peak
 
@@ -494,6 +527,9 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-streamed", action="store_true", help="skip the streamed-index measurement")
+    ap.add_argument("--streamed-steps", type=int, default=10)
+    ap.add_argument("--stage-bytes", type=int, default=0, help="streamed index: device staging bytes (0 = 2 slots)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-queries", type=int, default=400)
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)

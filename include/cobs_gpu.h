@@ -132,6 +132,16 @@ cobs_status cobs_device_index_download(const cobs_device_index *dix, cobs_index 
 /* Upload a host index to `device`; the index stays resident until freed. */
 cobs_status cobs_load_device(const cobs_index *ix, int device, void *stream, cobs_device_index **out);
 
+/* Streamed device index, for indexes larger than device memory (Sec. 2.3: the
+ * compact index is queried block by block from external memory).  The rows of
+ * `ix` are copied into pinned host memory owned by the returned object; the block
+ * table and permutation go to `device`.  Engines created on it copy each block's
+ * rows into a ring of device staging slots (cobs_engine_cfg.stage_bytes) on a
+ * second stream while the previous block is gathered, so a query batch reads the
+ * whole index over the host link once.  Only the batched and graph forms run on
+ * a streamed index (COBS_PLAIN: ARG).  Errors: ARG, OOM (pinned memory), CUDA. */
+cobs_status cobs_load_device_streamed(const cobs_index *ix, int device, void *stream, cobs_device_index **out);
+
 /* Save / load the library's own file format (header, block table, permutation,
  * per-document term counts, rows; little-endian).  load: FORMAT on a bad file. */
 cobs_status cobs_index_save(const cobs_index *ix, const char *path);
@@ -144,7 +154,8 @@ cobs_status cobs_index_info(const cobs_index *ix, cobs_params *params, uint64_t 
                             const cobs_block_info **blocks, const uint64_t **perm, const uint64_t **nterms,
                             const uint8_t **rows, uint64_t *rows_bytes);
 
-/* Inspect a device index (host copies of the table; device pointer to the rows). */
+/* Inspect a device index (host copies of the table; device pointer to the rows,
+ * or NULL for a streamed index, whose rows are in pinned host memory). */
 cobs_status cobs_device_index_info(const cobs_device_index *dix, cobs_params *params, uint64_t *n_docs,
                                    uint64_t *n_blocks, const cobs_block_info **blocks,
                                    const void **rows_dev, uint64_t *rows_bytes);
@@ -184,6 +195,9 @@ typedef struct cobs_engine_cfg {
                                  several tiles split queries of more than 4080 windows
                                  into parts of 4080 terms, summed before the threshold),
                                  1 = never, 2 = always */
+    uint64_t stage_bytes;     /* streamed index only: device bytes of the staging ring, split
+                                 into slots of the largest block's bytes (0 = two slots;
+                                 at least one slot, at most one per block) */
 } cobs_engine_cfg;
 
 cobs_status cobs_engine_create(cobs_device_index *dix, const cobs_engine_cfg *cfg, void *stream,
@@ -222,6 +236,7 @@ typedef struct cobs_query_stats {
     uint32_t slice_bytes, ctas_per_sm, l2_hints;
     uint32_t split_queries;   /* queries of the last batch that ran as split parts */
     double ms_host;           /* host time of the last query call: planning and enqueueing */
+    uint64_t h2d_index_bytes; /* streamed index: row bytes copied to the staging ring */
 } cobs_query_stats;
 cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out);
 
@@ -289,7 +304,7 @@ cobs_status cobs_serve_stop(cobs_server *srv, cobs_serve_stats *out);
  * shares the one scratch array and leaves its contents behind (each call clears
  * what must start at zero), so calls that overlap on the GPU -- on different
  * streams, or from different threads -- race with each other and give wrong
- * results: serialise them. */
+ * results: serialise them.  A streamed index is refused (ARG). */
 #define COBS_NOALLOC_MAX_WINDOWS 16384u
 #define COBS_NOALLOC_MAX_DOCS 131072u
 #define COBS_NOALLOC_MAX_ROW_LISTS 32u

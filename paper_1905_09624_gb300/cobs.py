@@ -57,7 +57,7 @@ class cobs_result(ctypes.Structure):
 class cobs_engine_cfg(ctypes.Structure):
     _fields_ = [("max_queries", ctypes.c_uint64), ("max_query_bytes", ctypes.c_uint64), ("max_hits", ctypes.c_uint64),
                 ("slice_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("l2_hints", ctypes.c_uint32),
-                ("split", ctypes.c_uint32)]
+                ("split", ctypes.c_uint32), ("stage_bytes", ctypes.c_uint64)]
 
 
 class cobs_query_stats(ctypes.Structure):
@@ -65,7 +65,8 @@ class cobs_query_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("row_bytes", ctypes.c_uint64), ("terms", ctypes.c_uint64),
                 ("n_tiles", ctypes.c_uint64), ("gather_launches", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("slice_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("l2_hints", ctypes.c_uint32),
-                ("split_queries", ctypes.c_uint32), ("ms_host", ctypes.c_double)]
+                ("split_queries", ctypes.c_uint32), ("ms_host", ctypes.c_double),
+                ("h2d_index_bytes", ctypes.c_uint64)]
 
 
 class cobs_serve_cfg(ctypes.Structure):
@@ -89,6 +90,7 @@ _PROTOS = {
     "cobs_build": (ctypes.c_int, [ctypes.POINTER(cobs_params), vp, vp, ctypes.c_uint64, ctypes.POINTER(vp)]),
     "cobs_device_index_download": (ctypes.c_int, [vp, ctypes.POINTER(vp)]),
     "cobs_load_device": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.POINTER(vp)]),
+    "cobs_load_device_streamed": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.POINTER(vp)]),
     "cobs_index_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
     "cobs_index_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(vp)]),
     "cobs_index_info": (ctypes.c_int, [vp, ctypes.POINTER(cobs_params), u64p, u64p,
@@ -285,6 +287,14 @@ class DeviceIndex:
         check(lib().cobs_load_device(host_index.h, device, stream, ctypes.byref(h)), "cobs_load_device")
         return DeviceIndex(h.value)
 
+    @staticmethod
+    def load_streamed(host_index: HostIndex, device=0, stream=None):
+        """cobs_load_device_streamed: rows in pinned host memory, streamed per batch."""
+        h = vp()
+        check(lib().cobs_load_device_streamed(host_index.h, device, stream, ctypes.byref(h)),
+              "cobs_load_device_streamed")
+        return DeviceIndex(h.value)
+
     def download(self) -> HostIndex:
         h = vp()
         check(lib().cobs_device_index_download(self.h, ctypes.byref(h)), "cobs_device_index_download")
@@ -315,9 +325,10 @@ class DeviceIndex:
 class Engine:
     """cobs_engine: reusable query workspace on one device index."""
 
-    def __init__(self, dix: DeviceIndex, stream=None, slice_bytes=0, ctas_per_sm=0, max_hits=0, l2_hints=0, split=0):
+    def __init__(self, dix: DeviceIndex, stream=None, slice_bytes=0, ctas_per_sm=0, max_hits=0, l2_hints=0, split=0,
+                 stage_bytes=0):
         self.dix = dix
-        cfg = cobs_engine_cfg(0, 0, max_hits, slice_bytes, ctas_per_sm, l2_hints, split)
+        cfg = cobs_engine_cfg(0, 0, max_hits, slice_bytes, ctas_per_sm, l2_hints, split, stage_bytes)
         h = vp()
         check(lib().cobs_engine_create(dix.h, ctypes.byref(cfg), stream, ctypes.byref(h)), "cobs_engine_create")
         self.h = h

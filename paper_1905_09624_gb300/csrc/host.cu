@@ -340,7 +340,9 @@ extern "C" cobs_status cobs_device_index_download(const cobs_device_index *dix, 
     ix->perm = dix->perm;
     ix->nterms = dix->nterms;
     ix->rows.resize(dix->rows_bytes);
-    if (dix->rows_bytes) {
+    if (dix->rows_bytes && dix->streamed) {
+        memcpy(ix->rows.data(), dix->host_rows.p, dix->rows_bytes);
+    } else if (dix->rows_bytes) {
         cudaError_t e = cudaMemcpy(ix->rows.data(), dix->rows.p, dix->rows_bytes, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) {
             delete ix;
@@ -362,7 +364,9 @@ extern "C" cobs_status cobs_build(const cobs_params *params, const uint8_t *docs
     return s;
 }
 
-extern "C" cobs_status cobs_load_device(const cobs_index *ix, int device, void *stream, cobs_device_index **out) {
+// Resident: rows copied to device memory.  Streamed: rows copied to pinned host
+// memory, streamed block by block by the engines.
+static cobs_status load_impl(const cobs_index *ix, int device, void *stream, bool streamed, cobs_device_index **out) {
     if (!ix || !out) return set_error(COBS_ERR_ARG, "NULL argument");
     TRY(check_params(&ix->params));
     CU(cudaSetDevice(device));
@@ -374,10 +378,18 @@ extern "C" cobs_status cobs_load_device(const cobs_index *ix, int device, void *
     dix->perm = ix->perm;
     dix->nterms = ix->nterms;
     dix->rows_bytes = ix->rows.size();
+    dix->streamed = streamed;
+    for (const auto &b : ix->blocks) dix->max_block_bytes = std::max<uint64_t>(dix->max_block_bytes, b.w * b.rowbytes);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = dix->rows.ensure(dix->rows_bytes);
-    if (e == cudaSuccess && dix->rows_bytes)
-        e = cudaMemcpyAsync(dix->rows.p, ix->rows.data(), dix->rows_bytes, cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaSuccess;
+    if (streamed) {
+        e = dix->host_rows.ensure(dix->rows_bytes);
+        if (e == cudaSuccess && dix->rows_bytes) memcpy(dix->host_rows.p, ix->rows.data(), dix->rows_bytes);
+    } else {
+        e = dix->rows.ensure(dix->rows_bytes);
+        if (e == cudaSuccess && dix->rows_bytes)
+            e = cudaMemcpyAsync(dix->rows.p, ix->rows.data(), dix->rows_bytes, cudaMemcpyHostToDevice, s);
+    }
     if (e != cudaSuccess) {
         delete dix;
         return set_error(e == cudaErrorMemoryAllocation ? COBS_ERR_OOM : COBS_ERR_CUDA, "load rows: %s",
@@ -390,6 +402,15 @@ extern "C" cobs_status cobs_load_device(const cobs_index *ix, int device, void *
     }
     *out = dix;
     return COBS_OK;
+}
+
+extern "C" cobs_status cobs_load_device(const cobs_index *ix, int device, void *stream, cobs_device_index **out) {
+    return load_impl(ix, device, stream, false, out);
+}
+
+extern "C" cobs_status cobs_load_device_streamed(const cobs_index *ix, int device, void *stream,
+                                                 cobs_device_index **out) {
+    return load_impl(ix, device, stream, true, out);
 }
 
 extern "C" void cobs_index_free(cobs_index *ix) { delete ix; }
@@ -422,7 +443,7 @@ extern "C" cobs_status cobs_device_index_info(const cobs_device_index *dix, cobs
     if (n_docs) *n_docs = dix->n_docs;
     if (n_blocks) *n_blocks = dix->blocks.size();
     if (blocks) *blocks = dix->blocks.data();
-    if (rows_dev) *rows_dev = dix->rows.p;
+    if (rows_dev) *rows_dev = dix->streamed ? nullptr : dix->rows.p;
     if (rows_bytes) *rows_bytes = dix->rows_bytes;
     return COBS_OK;
 }
@@ -495,8 +516,11 @@ static cobs_status ensure_slices(cobs_engine *eng, uint32_t lpq) {
     if (eng->slice_lpq == lpq && eng->n_slices) return COBS_OK;
     std::vector<SliceDesc> sl;
     const uint32_t S = 16 * lpq;
-    for (uint32_t b = 0; b < eng->dix->blocks.size(); b++)
+    eng->block_slice0.assign(1, 0u);
+    for (uint32_t b = 0; b < eng->dix->blocks.size(); b++) {
         for (uint32_t off = 0; off < eng->dix->blocks[b].rowbytes; off += S) sl.push_back(SliceDesc{b, off});
+        eng->block_slice0.push_back((uint32_t)sl.size());
+    }
     CU(eng->slices.ensure(std::max<size_t>(sl.size(), 1) * sizeof(SliceDesc)));
     if (!sl.empty())
         CU(cudaMemcpyAsync(eng->slices.p, sl.data(), sl.size() * sizeof(SliceDesc), cudaMemcpyHostToDevice,
@@ -546,6 +570,33 @@ extern "C" cobs_status cobs_engine_create(cobs_device_index *dix, const cobs_eng
     eng->hit_cap = eng->cfg.max_hits ? eng->cfg.max_hits : (1ULL << 20);
     for (auto &e : eng->ev) cudaEventCreate(&e);
     cudaEventCreateWithFlags(&eng->ev_done, cudaEventDisableTiming);
+    if (dix->streamed && !dix->blocks.empty()) {
+        // staging ring: slots of the largest block, one per block at most
+        const uint64_t slot = (dix->max_block_bytes + 255) / 256 * 256;
+        uint64_t ns = eng->cfg.stage_bytes ? eng->cfg.stage_bytes / std::max<uint64_t>(slot, 1) : 2;
+        ns = std::min<uint64_t>(ns, dix->blocks.size());
+        if (ns == 0) {
+            cobs_engine_free(eng);
+            return set_error(COBS_ERR_ARG, "stage_bytes %llu below one slot of %llu bytes",
+                             (unsigned long long)eng->cfg.stage_bytes, (unsigned long long)slot);
+        }
+        eng->n_stage = (uint32_t)ns;
+        eng->stage_slot_bytes = slot;
+        cudaError_t e = eng->stage.ensure(ns * slot);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&eng->copy_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&eng->ev_fork, cudaEventDisableTiming);
+        eng->ev_up.assign(ns, nullptr);
+        eng->ev_free.assign(ns, nullptr);
+        for (uint64_t i = 0; i < ns && e == cudaSuccess; i++) {
+            e = cudaEventCreateWithFlags(&eng->ev_up[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&eng->ev_free[i], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) {
+            cobs_engine_free(eng);
+            return set_error(e == cudaErrorMemoryAllocation ? COBS_ERR_OOM : COBS_ERR_CUDA, "staging ring: %s",
+                             cudaGetErrorString(e));
+        }
+    }
     cobs_status st = ensure_slices(eng, eng->lanes_per_query);
     if (st != COBS_OK) {
         cobs_engine_free(eng);
@@ -563,6 +614,15 @@ extern "C" void cobs_engine_free(cobs_engine *eng) {
     for (auto &e : eng->ev)
         if (e) cudaEventDestroy(e);
     if (eng->ev_done) cudaEventDestroy(eng->ev_done);
+    if (eng->copy_stream) {
+        cudaStreamSynchronize(eng->copy_stream);
+        cudaStreamDestroy(eng->copy_stream);
+    }
+    if (eng->ev_fork) cudaEventDestroy(eng->ev_fork);
+    for (auto e : eng->ev_up)
+        if (e) cudaEventDestroy(e);
+    for (auto e : eng->ev_free)
+        if (e) cudaEventDestroy(e);
     if (eng->own_stream) cudaStreamDestroy(eng->stream);
     delete eng;
 }
@@ -668,7 +728,9 @@ static cobs_status ensure_buffers(cobs_engine *eng, const BatchPlan &bp) {
     CU(eng->partials.ensure(bp.n_parts * eng->dix->n_docs * 2));
     CU(eng->ell.ensure(n * 4));
     CU(eng->minsc.ensure(n * 4));
-    CU(eng->qcount.ensure(n * 4 + 64 * 8));  // qcount, then the counters (one memset clears both)
+    // qcount, then the counters (one memset clears both): [0] hits, [1..14] work
+    // counters, [15] big segments, then 4 per block for a streamed index
+    CU(eng->qcount.ensure(n * 4 + (64 + 4 * nb) * 8));
     CU(eng->qcursor.ensure(n * 4));
     CU(eng->biglist.ensure(n * 4));
     CU(eng->hitoff.ensure((n + 1) * 8));
@@ -708,12 +770,15 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
     const uint4 *items = (const uint4 *)(plan + n * 16);
     const uint4 *split = items + bp.items.size();
     unsigned long long *ctr = counters_of(eng, n);
+    const uint64_t n_ctr = 16 + (dix->streamed ? 4 * dix->blocks.size() : 0);
     eng->stat_launches = 0;
     eng->stat_gather_launches = 0;
     eng->stat_tiles = 0;
+    eng->stat_h2d_index_bytes = 0;
 
     if (timed) CU(cudaEventRecord(eng->ev[0], s));
-    CU(cudaMemsetAsync(eng->qcount.p, 0, (uint8_t *)(ctr + 16) - eng->qcount.as<uint8_t>(), s));
+    if (dix->streamed) CU(cudaEventRecord(eng->ev_fork, s));  // the copy stream joins here
+    CU(cudaMemsetAsync(eng->qcount.p, 0, (uint8_t *)(ctr + n_ctr) - eng->qcount.as<uint8_t>(), s));
     CU(cudaMemcpyAsync(plan, eng->pin_plan.p, plan_bytes(bp), cudaMemcpyHostToDevice, s));
 
     TermsArgs ta{};
@@ -781,39 +846,69 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
         if (timed) CU(cudaEventRecord(eng->ev[1], s));
         const uint32_t qpw = 32 / eng->lanes_per_query;
         const uint32_t grid = (uint32_t)eng->n_sm * eng->ctas_per_sm;
-        for (size_t c = 0; c < bp.classes.size(); c++) {
-            const BatchPlan::Class &cl = bp.classes[c];
-            GatherArgs ga{};
-            ga.rows = dix->rows.as<uint8_t>();
-            ga.blocks = dix->dblocks.as<DevBlock>();
-            ga.perm = dix->dperm.as<uint32_t>();
-            ga.rows_idx = eng->rows_idx.as<uint32_t>();
-            ga.tcap = bp.tcap;
-            ga.term_base = term_base;
-            ga.ell = eng->ell.as<uint32_t>();
-            ga.thr = d_thr;
-            ga.items = items + cl.begin;
-            ga.n_queries = cl.count;
-            ga.h = P.num_hashes;
-            ga.slices = eng->slices.as<SliceDesc>();
-            ga.n_slices = eng->n_slices;
-            ga.n_groups = (cl.count + qpw - 1) / qpw;
-            ga.work_counter = ctr + 1 + (c % 14);  // ctr[15] is the big-segment count
-            ga.hit_count = ctr;
-            ga.qcount = eng->qcount.as<uint32_t>();
-            ga.raw_q = eng->raw_q.as<uint32_t>();
-            ga.raw_key = eng->raw_key.as<unsigned long long>();
-            ga.hit_cap = eng->hit_cap;
-            // l2_hints: 1 none, 2 row indices evict-first, 3 + index rows evict-last, 4 rows evict-last only
-            ga.l2_idx_policy = (eng->l2_hints == 2 || eng->l2_hints == 3) ? 1u : 0u;
-            ga.l2_row_policy = (eng->l2_hints == 3 || eng->l2_hints == 4) ? 2u : 0u;
-            ga.partials = eng->partials.as<uint16_t>();
-            ga.n_docs = (uint32_t)dix->n_docs;
-            if (ga.n_slices == 0 || ga.n_groups == 0) continue;
-            launch_gather_batched_L(ga, eng->lanes_per_query, cl.L, grid, s);
-            eng->stat_launches += 1;
-            eng->stat_gather_launches += 1;
-            eng->stat_tiles += (uint64_t)ga.n_slices * ga.n_groups;
+        // one gather launch per counter class over slices [sl0, sl0 + nsl); rows
+        // of block b are read at rows + row_offset_b
+        auto gather_classes = [&](const uint8_t *rows, uint32_t sl0, uint32_t nsl, unsigned long long *wctr) {
+            for (size_t c = 0; c < bp.classes.size(); c++) {
+                const BatchPlan::Class &cl = bp.classes[c];
+                GatherArgs ga{};
+                ga.rows = rows;
+                ga.blocks = dix->dblocks.as<DevBlock>();
+                ga.perm = dix->dperm.as<uint32_t>();
+                ga.rows_idx = eng->rows_idx.as<uint32_t>();
+                ga.tcap = bp.tcap;
+                ga.term_base = term_base;
+                ga.ell = eng->ell.as<uint32_t>();
+                ga.thr = d_thr;
+                ga.items = items + cl.begin;
+                ga.n_queries = cl.count;
+                ga.h = P.num_hashes;
+                ga.slices = eng->slices.as<SliceDesc>() + sl0;
+                ga.n_slices = nsl;
+                ga.n_groups = (cl.count + qpw - 1) / qpw;
+                ga.work_counter = wctr + c;
+                ga.hit_count = ctr;
+                ga.qcount = eng->qcount.as<uint32_t>();
+                ga.raw_q = eng->raw_q.as<uint32_t>();
+                ga.raw_key = eng->raw_key.as<unsigned long long>();
+                ga.hit_cap = eng->hit_cap;
+                // l2_hints: 1 none, 2 row indices evict-first, 3 + index rows evict-last, 4 rows evict-last only
+                ga.l2_idx_policy = (eng->l2_hints == 2 || eng->l2_hints == 3) ? 1u : 0u;
+                ga.l2_row_policy = (eng->l2_hints == 3 || eng->l2_hints == 4) ? 2u : 0u;
+                ga.partials = eng->partials.as<uint16_t>();
+                ga.n_docs = (uint32_t)dix->n_docs;
+                if (ga.n_slices == 0 || ga.n_groups == 0) continue;
+                launch_gather_batched_L(ga, eng->lanes_per_query, cl.L, grid, s);
+                eng->stat_launches += 1;
+                eng->stat_gather_launches += 1;
+                eng->stat_tiles += (uint64_t)ga.n_slices * ga.n_groups;
+            }
+        };
+        if (!dix->streamed) {
+            gather_classes(dix->rows.as<uint8_t>(), 0, eng->n_slices, ctr + 1);  // classes <= 4 < 15
+        } else {
+            // Block b: the copy stream fills slot b mod S once the gathers of block
+            // b - S have read it; the engine stream gathers block b once it is in.
+            const uint32_t nb = (uint32_t)dix->blocks.size();
+            CU(cudaStreamWaitEvent(eng->copy_stream, eng->ev_fork, 0));
+            for (uint32_t b = 0; b < nb; b++) {
+                const uint32_t slot = b % eng->n_stage;
+                const cobs_block_info &B = dix->blocks[b];
+                const uint64_t bytes = B.w * B.rowbytes;
+                uint8_t *dst = eng->stage.as<uint8_t>() + slot * eng->stage_slot_bytes;
+                if (b >= eng->n_stage) CU(cudaStreamWaitEvent(eng->copy_stream, eng->ev_free[slot], 0));
+                if (bytes)
+                    CU(cudaMemcpyAsync(dst, dix->host_rows.as<uint8_t>() + B.row_offset, bytes,
+                                       cudaMemcpyHostToDevice, eng->copy_stream));
+                CU(cudaEventRecord(eng->ev_up[slot], eng->copy_stream));
+                CU(cudaStreamWaitEvent(s, eng->ev_up[slot], 0));
+                // the kernels add row_offset_b to the rows pointer: shift the slot back by it
+                const uint8_t *rows = (const uint8_t *)((uintptr_t)dst - (uintptr_t)B.row_offset);
+                gather_classes(rows, eng->block_slice0[b], eng->block_slice0[b + 1] - eng->block_slice0[b],
+                               ctr + 16 + 4 * b);
+                CU(cudaEventRecord(eng->ev_free[slot], s));
+                eng->stat_h2d_index_bytes += bytes;
+            }
         }
         if (!bp.split.empty()) {
             SplitArgs sa{};
@@ -901,6 +996,8 @@ cobs_status engine_query(cobs_engine *eng, const uint8_t *d_bytes, const uint64_
     if (flags != COBS_PLAIN && flags != COBS_BATCHED && flags != COBS_GRAPH && flags != (COBS_GRAPH | COBS_BATCHED))
         return set_error(COBS_ERR_ARG, "flags must be COBS_PLAIN, COBS_BATCHED or COBS_GRAPH");
     if (n >= 0x7FFFFFFFULL) return set_error(COBS_ERR_ARG, "too many queries in one batch");
+    if (eng->dix->streamed && flags == COBS_PLAIN)
+        return set_error(COBS_ERR_ARG, "a streamed index runs the batched or graph form only");
     const auto t_host = std::chrono::steady_clock::now();
     CU(cudaSetDevice(eng->dix->device));
     TRY(make_plan(eng, h_off, n, flags != COBS_PLAIN, eng->bp));
@@ -1138,6 +1235,7 @@ extern "C" cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out
     out->l2_hints = eng->l2_hints;
     out->split_queries = (uint32_t)eng->bp.split.size();
     out->ms_host = eng->stat_host_ms;
+    out->h2d_index_bytes = eng->stat_h2d_index_bytes;
     return COBS_OK;
 }
 

@@ -105,6 +105,10 @@ struct cobs_device_index {
     uint64_t rows_bytes = 0;
     uint32_t n_cols = 0;  // 16-byte columns over all blocks (plain kernel)
     cobs::DevBuf rows, dblocks, dperm, col_block, col_byte;
+    // streamed index: rows in pinned host memory, copied block by block per batch
+    bool streamed = false;
+    cobs::PinBuf host_rows;
+    uint64_t max_block_bytes = 0;
 };
 
 struct cobs_engine {
@@ -129,6 +133,16 @@ struct cobs_engine {
     cobs::DevBuf scores;                      // plain form, per sorted position
     cobs::DevBuf slices;
     uint32_t n_slices = 0, slice_lpq = 0;
+    std::vector<uint32_t> block_slice0;       // per block: first slice (n_blocks + 1 entries)
+
+    // streamed index: staging ring of device slots, filled on a second stream
+    cobs::DevBuf stage;
+    uint32_t n_stage = 0;
+    uint64_t stage_slot_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_up, ev_free;  // per slot: rows copied / slot read by its gathers
+    uint64_t stat_h2d_index_bytes = 0;
     cobs::PinBuf pin_plan, pin_count, pin_in;
 
     cobs::BatchPlan bp;

@@ -85,6 +85,7 @@ extern "C" cobs_status cobs_query_one_noalloc(cobs_device_index *dix, const uint
     if (!dix || !out_meta_dev || (len && !query_dev) || (dix->n_docs && (!out_ids_dev || !out_scores_dev)))
         return set_error(COBS_ERR_ARG, "NULL argument");
     if (thr_permille == 0 || thr_permille > 1000) return set_error(COBS_ERR_ARG, "threshold must be 1..1000 permille");
+    if (dix->streamed) return set_error(COBS_ERR_ARG, "this entry point needs a resident index");
     const cobs_params &P = dix->params;
     const uint64_t np = len >= P.q ? len - P.q + 1 : 0;
     if (np > (P.score_bits == 16 ? 0xFFFFULL : 0xFFFFFFFFULL))
