@@ -570,6 +570,17 @@ extern "C" cobs_status cobs_engine_create(cobs_device_index *dix, const cobs_eng
     eng->hit_cap = eng->cfg.max_hits ? eng->cfg.max_hits : (1ULL << 20);
     for (auto &e : eng->ev) cudaEventCreate(&e);
     cudaEventCreateWithFlags(&eng->ev_done, cudaEventDisableTiming);
+    {
+        cudaError_t e = cudaEventCreateWithFlags(&eng->ev_terms, cudaEventDisableTiming);
+        for (int c = 0; c < cobs_engine::MAX_CLASSES && e == cudaSuccess; c++) {
+            e = cudaStreamCreateWithFlags(&eng->cls_stream[c], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&eng->ev_cls[c], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) {
+            cobs_engine_free(eng);
+            return set_error(COBS_ERR_CUDA, "class streams: %s", cudaGetErrorString(e));
+        }
+    }
     if (dix->streamed && !dix->blocks.empty()) {
         // staging ring: slots of the largest block, one per block at most
         const uint64_t slot = (dix->max_block_bytes + 255) / 256 * 256;
@@ -586,11 +597,11 @@ extern "C" cobs_status cobs_engine_create(cobs_device_index *dix, const cobs_eng
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&eng->copy_stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&eng->ev_fork, cudaEventDisableTiming);
         eng->ev_up.assign(ns, nullptr);
-        eng->ev_free.assign(ns, nullptr);
-        for (uint64_t i = 0; i < ns && e == cudaSuccess; i++) {
+        eng->ev_free.assign(ns * cobs_engine::MAX_CLASSES, nullptr);
+        for (uint64_t i = 0; i < ns && e == cudaSuccess; i++)
             e = cudaEventCreateWithFlags(&eng->ev_up[i], cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&eng->ev_free[i], cudaEventDisableTiming);
-        }
+        for (size_t i = 0; i < eng->ev_free.size() && e == cudaSuccess; i++)
+            e = cudaEventCreateWithFlags(&eng->ev_free[i], cudaEventDisableTiming);
         if (e != cudaSuccess) {
             cobs_engine_free(eng);
             return set_error(e == cudaErrorMemoryAllocation ? COBS_ERR_OOM : COBS_ERR_CUDA, "staging ring: %s",
@@ -619,6 +630,14 @@ extern "C" void cobs_engine_free(cobs_engine *eng) {
         cudaStreamDestroy(eng->copy_stream);
     }
     if (eng->ev_fork) cudaEventDestroy(eng->ev_fork);
+    if (eng->ev_terms) cudaEventDestroy(eng->ev_terms);
+    for (int c = 0; c < cobs_engine::MAX_CLASSES; c++) {
+        if (eng->cls_stream[c]) {
+            cudaStreamSynchronize(eng->cls_stream[c]);
+            cudaStreamDestroy(eng->cls_stream[c]);
+        }
+        if (eng->ev_cls[c]) cudaEventDestroy(eng->ev_cls[c]);
+    }
     for (auto e : eng->ev_up)
         if (e) cudaEventDestroy(e);
     for (auto e : eng->ev_free)
@@ -846,6 +865,15 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
         if (timed) CU(cudaEventRecord(eng->ev[1], s));
         const uint32_t qpw = 32 / eng->lanes_per_query;
         const uint32_t grid = (uint32_t)eng->n_sm * eng->ctas_per_sm;
+        // several counter classes: each on its own stream, forked after the terms
+        const uint32_t n_cls = (uint32_t)bp.classes.size();
+        if (n_cls > (uint32_t)cobs_engine::MAX_CLASSES) return set_error(COBS_ERR_ARG, "more than 4 counter classes");
+        const bool multi = n_cls > 1;
+        auto gs = [&](size_t c) { return multi ? eng->cls_stream[c] : s; };
+        if (multi) {
+            CU(cudaEventRecord(eng->ev_terms, s));
+            for (uint32_t c = 0; c < n_cls; c++) CU(cudaStreamWaitEvent(gs(c), eng->ev_terms, 0));
+        }
         // one gather launch per counter class over slices [sl0, sl0 + nsl); rows
         // of block b are read at rows + row_offset_b
         auto gather_classes = [&](const uint8_t *rows, uint32_t sl0, uint32_t nsl, unsigned long long *wctr) {
@@ -878,7 +906,7 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
                 ga.partials = eng->partials.as<uint16_t>();
                 ga.n_docs = (uint32_t)dix->n_docs;
                 if (ga.n_slices == 0 || ga.n_groups == 0) continue;
-                launch_gather_batched_L(ga, eng->lanes_per_query, cl.L, grid, s);
+                launch_gather_batched_L(ga, eng->lanes_per_query, cl.L, grid, gs(c));
                 eng->stat_launches += 1;
                 eng->stat_gather_launches += 1;
                 eng->stat_tiles += (uint64_t)ga.n_slices * ga.n_groups;
@@ -887,27 +915,38 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
         if (!dix->streamed) {
             gather_classes(dix->rows.as<uint8_t>(), 0, eng->n_slices, ctr + 1);  // classes <= 4 < 15
         } else {
-            // Block b: the copy stream fills slot b mod S once the gathers of block
-            // b - S have read it; the engine stream gathers block b once it is in.
+            // Block b: the copy stream fills slot b mod S once every class's gathers
+            // of block b - S have read it; each class gathers block b once it is in.
             const uint32_t nb = (uint32_t)dix->blocks.size();
+            const uint32_t MC = (uint32_t)cobs_engine::MAX_CLASSES;
             CU(cudaStreamWaitEvent(eng->copy_stream, eng->ev_fork, 0));
             for (uint32_t b = 0; b < nb; b++) {
                 const uint32_t slot = b % eng->n_stage;
                 const cobs_block_info &B = dix->blocks[b];
                 const uint64_t bytes = B.w * B.rowbytes;
                 uint8_t *dst = eng->stage.as<uint8_t>() + slot * eng->stage_slot_bytes;
-                if (b >= eng->n_stage) CU(cudaStreamWaitEvent(eng->copy_stream, eng->ev_free[slot], 0));
+                if (b >= eng->n_stage)
+                    for (uint32_t c = 0; c < std::max(n_cls, 1u); c++)
+                        CU(cudaStreamWaitEvent(eng->copy_stream, eng->ev_free[slot * MC + c], 0));
                 if (bytes)
                     CU(cudaMemcpyAsync(dst, dix->host_rows.as<uint8_t>() + B.row_offset, bytes,
                                        cudaMemcpyHostToDevice, eng->copy_stream));
                 CU(cudaEventRecord(eng->ev_up[slot], eng->copy_stream));
-                CU(cudaStreamWaitEvent(s, eng->ev_up[slot], 0));
+                for (uint32_t c = 0; c < std::max(n_cls, 1u); c++) CU(cudaStreamWaitEvent(gs(c), eng->ev_up[slot], 0));
                 // the kernels add row_offset_b to the rows pointer: shift the slot back by it
                 const uint8_t *rows = (const uint8_t *)((uintptr_t)dst - (uintptr_t)B.row_offset);
                 gather_classes(rows, eng->block_slice0[b], eng->block_slice0[b + 1] - eng->block_slice0[b],
                                ctr + 16 + 4 * b);
-                CU(cudaEventRecord(eng->ev_free[slot], s));
+                for (uint32_t c = 0; c < std::max(n_cls, 1u); c++)
+                    CU(cudaEventRecord(eng->ev_free[slot * MC + c], gs(c)));
                 eng->stat_h2d_index_bytes += bytes;
+            }
+            if (nb) CU(cudaStreamWaitEvent(s, eng->ev_up[(nb - 1) % eng->n_stage], 0));  // join the copy stream
+        }
+        if (multi) {  // join the class streams
+            for (uint32_t c = 0; c < n_cls; c++) {
+                CU(cudaEventRecord(eng->ev_cls[c], gs(c)));
+                CU(cudaStreamWaitEvent(s, eng->ev_cls[c], 0));
             }
         }
         if (!bp.split.empty()) {

@@ -141,7 +141,13 @@ struct cobs_engine {
     uint64_t stage_slot_bytes = 0;
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_fork = nullptr;
-    std::vector<cudaEvent_t> ev_up, ev_free;  // per slot: rows copied / slot read by its gathers
+    std::vector<cudaEvent_t> ev_up, ev_free;  // per slot: rows copied / per (slot, class): slot read
+    // counter classes of a batch run on their own streams, so a class of a few
+    // long queries overlaps the others instead of running alone
+    static constexpr int MAX_CLASSES = 4;
+    cudaStream_t cls_stream[MAX_CLASSES] = {};
+    cudaEvent_t ev_cls[MAX_CLASSES] = {};
+    cudaEvent_t ev_terms = nullptr;
     uint64_t stat_h2d_index_bytes = 0;
     cobs::PinBuf pin_plan, pin_count, pin_in;
 
