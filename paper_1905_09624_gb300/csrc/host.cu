@@ -683,10 +683,24 @@ static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n
         bp.max_npos = std::max(bp.max_npos, np);
     }
     if (bp.tcap == 0) bp.tcap = TERM_ALIGN;
+    // queries by windows, longest first, ties in input order: a stable LSD radix
+    // sort on the complemented window count (below 2^24), two 12-bit digits
     std::vector<uint32_t> order(n);
     std::iota(order.begin(), order.end(), 0u);
     auto longer = [&](uint32_t a, uint32_t b) { return bp.npos[a] > bp.npos[b]; };
-    if (!std::is_sorted(order.begin(), order.end(), longer)) std::stable_sort(order.begin(), order.end(), longer);
+    if (!std::is_sorted(order.begin(), order.end(), longer)) {
+        std::vector<uint32_t> tmp(n);
+        std::vector<uint32_t> cnt(4097);
+        for (int pass = 0; pass < 2; pass++) {
+            const int sh = 12 * pass;
+            auto digit = [&](uint32_t q) { return (uint32_t)(((~bp.npos[q] & 0xFFFFFFu) >> sh) & 0xFFFu); };
+            std::fill(cnt.begin(), cnt.end(), 0u);
+            for (uint64_t i = 0; i < n; i++) cnt[digit(order[i]) + 1]++;
+            for (int d = 0; d < 4096; d++) cnt[d + 1] += cnt[d];
+            for (uint64_t i = 0; i < n; i++) tmp[cnt[digit(order[i])]++] = order[i];
+            order.swap(tmp);
+        }
+    }
     // Work items.  A batch too small to give every resident warp several tiles
     // splits its long queries into items of SPLIT_TERMS terms (h == 1 only), so
     // one long query no longer runs on a single warp per slice.
