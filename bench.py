@@ -460,6 +460,37 @@ def run_gpu(args):
                     "stage_bytes": n_slots * slot, "index_bytes": info["rows_bytes"],
                     "results_identical_to_resident": bool(same)}
         del seng, sdix
+    # ---- multi-index querying: a view over two indexes of half the documents each
+    multi = None
+    if not args.skip_multi and wl.n_docs >= 2:
+        half = wl.n_docs // 2
+        parts = []
+        for lo, hi in ((0, half), (half, wl.n_docs)):
+            o = wl.doc_off[lo:hi + 1] - wl.doc_off[lo]
+            parts.append(cobs.DeviceIndex.build(P, wl.docs[int(wl.doc_off[lo]):int(wl.doc_off[hi])], o,
+                                                device=local))
+        view = cobs.DeviceIndex.multi(parts)
+        meng = cobs.Engine(view, stream=sh, slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm)
+        for _ in range(3):
+            flush_l2()
+            meng.query_device(d_q, d_off, wl.q_off, d_thr, form)
+            meng.stats()
+        m_ms, m_terms, m_rows = [], 0, 0
+        for i in range(args.streamed_steps):
+            flush_l2()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            meng.query_device(d_q, d_off, wl.q_off, d_thr, form)
+            e1.record(stream)
+            mst = meng.stats()
+            m_ms.append(e0.elapsed_time(e1))
+            m_terms += mst["terms"]
+            m_rows += mst["row_bytes"]
+        mm = float(np.mean(m_ms))
+        multi = {"value": m_terms / args.streamed_steps / (mm / 1e3), "unit": UNIT, "ms_per_step": mm,
+                 "steps": args.streamed_steps, "parts": 2, "blocks": len(view.info()["blocks"]),
+                 "row_gbs_logical": m_rows / args.streamed_steps / (mm / 1e3) / 1e9}
+        del meng, view, parts
     sampler.stop()
     clocks = sampler.summary(t_wall0, t_wall1)
 
@@ -492,7 +523,7 @@ def run_gpu(args):
                      "gbs_with_h2d": int(wl.doc_off[-1]) / build_h2d_s / 1e9,
                      "index_bytes": info["rows_bytes"], "blocks": len(info["blocks"])},
            "speedup_batched_over_plain": (value / plain["value"]) if plain else None,
-           "streamed": streamed}
+           "streamed": streamed, "multi_index": multi}
     if plain:
         out["plain"]["frac_of_hbm_peak"] = plain["row_gbs_logical"] / peak
 
@@ -528,7 +559,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-streamed", action="store_true", help="skip the streamed-index measurement")
-    ap.add_argument("--streamed-steps", type=int, default=10)
+    ap.add_argument("--streamed-steps", type=int, default=10, help="timed steps of the streamed and multi-index runs")
+    ap.add_argument("--skip-multi", action="store_true", help="skip the multi-index measurement")
     ap.add_argument("--stage-bytes", type=int, default=0, help="streamed index: device staging bytes (0 = 2 slots)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-queries", type=int, default=400)

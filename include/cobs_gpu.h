@@ -60,6 +60,9 @@ typedef struct cobs_params {
     uint32_t score_bits;  /* 16 or 32: width of the reported score counters */
     double fpr;           /* target false-positive rate p of every filter, 0 < p < 1 */
     uint64_t block_docs;  /* B documents per block (compact); 0 = classic, one block in input order */
+    uint64_t width;       /* 0 = every block's Bloom size from the Sec. 2.1 bound; else every block
+                             gets w = width (classic indexes built over batches of documents with
+                             one common w merge by concatenation, Sec. 2.3); at most 2^32 - 1 */
 } cobs_params;
 
 /* One block of the index; same meaning on host and device.  Sec. 2.2: documents at
@@ -142,10 +145,35 @@ cobs_status cobs_load_device(const cobs_index *ix, int device, void *stream, cob
  * a streamed index (COBS_PLAIN: ARG).  Errors: ARG, OOM (pinned memory), CUDA. */
 cobs_status cobs_load_device_streamed(const cobs_index *ix, int device, void *stream, cobs_device_index **out);
 
+/* Multi-index querying (Sec. 4: a front end queries several index files at once
+ * and selects datasets by the indexes it combines): a device index that borrows
+ * the rows of n_parts device indexes (no copy) and presents their blocks as one
+ * index, queried by the same kernels in one launch sequence.  Document j of part
+ * i gets id offset_i + j, offset_i = the documents of parts 0..i-1; every
+ * document scores exactly as on its own part.  Parts must be on one device,
+ * agree in term kind, q and number of hashes, and not be streamed (ARG
+ * otherwise); a part may itself be a multi-index.  score_bits is the widest of
+ * the parts.  The parts must outlive the view; free it with
+ * cobs_device_index_free.  cobs_device_index_download of a view returns the
+ * merged host index (cobs_index_merge layout: the parts' blocks in order). */
+cobs_status cobs_multi_index_create(cobs_device_index *const *parts, uint64_t n_parts, cobs_device_index **out);
+
 /* Save / load the library's own file format (header, block table, permutation,
  * per-document term counts, rows; little-endian).  load: FORMAT on a bad file. */
 cobs_status cobs_index_save(const cobs_index *ix, const char *path);
 cobs_status cobs_index_load(const char *path, cobs_index **out);
+
+/* Merge two host indexes into a new one (Sec. 2.3: classic indexes with the same
+ * parameters are concatenated; compact ones stay separate sub-indexes).  The
+ * documents of b follow those of a: document j of b gets id n_docs(a) + j.
+ *  - a and b classic (block_docs 0, one block each) with the same w: one classic
+ *    block whose rows are a's document bits followed by b's -- bit-identical to
+ *    the classic index built over both document lists with width = w;
+ *  - otherwise: a's blocks, then b's (row offsets and sorted positions shifted);
+ *    queries score every document exactly as on a and b separately.
+ * term_kind, q and num_hashes must agree (ARG); score_bits is the wider of the
+ * two.  Host memory only; a and b are unchanged. */
+cobs_status cobs_index_merge(const cobs_index *a, const cobs_index *b, cobs_index **out);
 
 /* Inspect a host index.  Pointers stay valid until cobs_index_free.
  * perm[i] = original id of the document at sorted position i;
@@ -155,7 +183,8 @@ cobs_status cobs_index_info(const cobs_index *ix, cobs_params *params, uint64_t 
                             const uint8_t **rows, uint64_t *rows_bytes);
 
 /* Inspect a device index (host copies of the table; device pointer to the rows,
- * or NULL for a streamed index, whose rows are in pinned host memory). */
+ * or NULL for a streamed index, whose rows are in pinned host memory, and for a
+ * multi-index view, whose rows stay in its parts). */
 cobs_status cobs_device_index_info(const cobs_device_index *dix, cobs_params *params, uint64_t *n_docs,
                                    uint64_t *n_blocks, const cobs_block_info **blocks,
                                    const void **rows_dev, uint64_t *rows_bytes);

@@ -37,7 +37,8 @@ vp = ctypes.c_void_p
 
 class cobs_params(ctypes.Structure):
     _fields_ = [("term_kind", ctypes.c_uint32), ("q", ctypes.c_uint32), ("num_hashes", ctypes.c_uint32),
-                ("score_bits", ctypes.c_uint32), ("fpr", ctypes.c_double), ("block_docs", ctypes.c_uint64)]
+                ("score_bits", ctypes.c_uint32), ("fpr", ctypes.c_double), ("block_docs", ctypes.c_uint64),
+                ("width", ctypes.c_uint64)]
 
 
 class cobs_block_info(ctypes.Structure):
@@ -91,6 +92,8 @@ _PROTOS = {
     "cobs_device_index_download": (ctypes.c_int, [vp, ctypes.POINTER(vp)]),
     "cobs_load_device": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.POINTER(vp)]),
     "cobs_load_device_streamed": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.POINTER(vp)]),
+    "cobs_multi_index_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_uint64, ctypes.POINTER(vp)]),
+    "cobs_index_merge": (ctypes.c_int, [vp, vp, ctypes.POINTER(vp)]),
     "cobs_index_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
     "cobs_index_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(vp)]),
     "cobs_index_info": (ctypes.c_int, [vp, ctypes.POINTER(cobs_params), u64p, u64p,
@@ -167,8 +170,8 @@ def _ptr(a):
     return a.ctypes.data
 
 
-def make_params(term_kind=0, q=31, num_hashes=1, fpr=0.3, block_docs=0, score_bits=32, **_ignored):
-    return cobs_params(term_kind, q, num_hashes, score_bits, fpr, block_docs)
+def make_params(term_kind=0, q=31, num_hashes=1, fpr=0.3, block_docs=0, score_bits=32, width=0, **_ignored):
+    return cobs_params(term_kind, q, num_hashes, score_bits, fpr, block_docs, width)
 
 
 def result_to_python(res_ptr):
@@ -251,6 +254,12 @@ class HostIndex:
         check(lib().cobs_index_load(path.encode(), ctypes.byref(h)), "cobs_index_load")
         return HostIndex(h.value)
 
+    def merge(self, other):
+        """cobs_index_merge: self's documents, then other's (ids shifted by self's count)."""
+        h = vp()
+        check(lib().cobs_index_merge(self.h, other.h, ctypes.byref(h)), "cobs_index_merge")
+        return HostIndex(h.value)
+
 
 class DeviceIndex:
     """cobs_device_index (resident in HBM)."""
@@ -286,6 +295,16 @@ class DeviceIndex:
         h = vp()
         check(lib().cobs_load_device(host_index.h, device, stream, ctypes.byref(h)), "cobs_load_device")
         return DeviceIndex(h.value)
+
+    @staticmethod
+    def multi(parts):
+        """cobs_multi_index_create: one index over several resident ones (borrowed rows)."""
+        arr = (vp * len(parts))(*[p.h for p in parts])
+        h = vp()
+        check(lib().cobs_multi_index_create(arr, len(parts), ctypes.byref(h)), "cobs_multi_index_create")
+        view = DeviceIndex(h.value)
+        view._parts = list(parts)  # the view borrows their rows
+        return view
 
     @staticmethod
     def load_streamed(host_index: HostIndex, device=0, stream=None):

@@ -66,6 +66,7 @@ static cobs_status check_params(const cobs_params *P) {
     if (P->num_hashes < 1 || P->num_hashes > 16) return set_error(COBS_ERR_ARG, "num_hashes must be 1..16");
     if (!(P->fpr > 0.0 && P->fpr < 1.0)) return set_error(COBS_ERR_ARG, "fpr must be in (0, 1)");
     if (P->score_bits != 16 && P->score_bits != 32) return set_error(COBS_ERR_ARG, "score_bits must be 16 or 32");
+    if (P->width > 0xFFFFFFFFULL) return set_error(COBS_ERR_ARG, "width must be below 2^32");
     return COBS_OK;
 }
 
@@ -87,7 +88,7 @@ static cobs_status plan_index(const cobs_params &P, const std::vector<uint64_t> 
         b.doc_begin = begin;
         b.n_docs = std::min(B, n - begin);
         for (uint64_t j = 0; j < b.n_docs; j++) b.max_terms = std::max(b.max_terms, v[perm[begin + j]]);
-        b.w = cobs_bloom_width(P.num_hashes, b.max_terms, P.fpr);
+        b.w = P.width ? P.width : cobs_bloom_width(P.num_hashes, b.max_terms, P.fpr);
         if (b.w > 0xFFFFFFFFULL) return set_error(COBS_ERR_ARG, "block %llu needs %llu rows (limit 2^32-1)",
                                                   (unsigned long long)blocks.size(), (unsigned long long)b.w);
         b.rowbytes = (b.n_docs + 127) / 128 * 16;
@@ -111,7 +112,7 @@ static cobs_status upload_tables(cobs_device_index *dix, cudaStream_t s) {
     std::vector<uint32_t> cb, cy;
     for (uint64_t b = 0; b < nb; b++) {
         const cobs_block_info &B = dix->blocks[b];
-        db[b].row_offset = B.row_offset;
+        db[b].row_offset = dix->dev_row_offset.empty() ? B.row_offset : dix->dev_row_offset[b];
         db[b].barrett_m = barrett_m_of(B.w);
         db[b].w = (uint32_t)B.w;
         db[b].rowbytes = (uint32_t)B.rowbytes;
@@ -342,6 +343,16 @@ extern "C" cobs_status cobs_device_index_download(const cobs_device_index *dix, 
     ix->rows.resize(dix->rows_bytes);
     if (dix->rows_bytes && dix->streamed) {
         memcpy(ix->rows.data(), dix->host_rows.p, dix->rows_bytes);
+    } else if (dix->rows_bytes && dix->rows_view) {
+        for (size_t b = 0; b < dix->blocks.size(); b++) {
+            const cobs_block_info &B = dix->blocks[b];
+            cudaError_t e = cudaMemcpy(ix->rows.data() + B.row_offset, dix->rows_view + dix->dev_row_offset[b],
+                                       B.w * B.rowbytes, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                delete ix;
+                return set_error(COBS_ERR_CUDA, "download rows: %s", cudaGetErrorString(e));
+            }
+        }
     } else if (dix->rows_bytes) {
         cudaError_t e = cudaMemcpy(ix->rows.data(), dix->rows.p, dix->rows_bytes, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) {
@@ -413,6 +424,61 @@ extern "C" cobs_status cobs_load_device_streamed(const cobs_index *ix, int devic
     return load_impl(ix, device, stream, true, out);
 }
 
+extern "C" cobs_status cobs_multi_index_create(cobs_device_index *const *parts, uint64_t n_parts,
+                                               cobs_device_index **out) {
+    if (!parts || !n_parts || !out) return set_error(COBS_ERR_ARG, "NULL argument");
+    for (uint64_t i = 0; i < n_parts; i++) {
+        const cobs_device_index *p = parts[i];
+        if (!p) return set_error(COBS_ERR_ARG, "part %llu is NULL", (unsigned long long)i);
+        if (p->streamed) return set_error(COBS_ERR_ARG, "part %llu is streamed; parts must be resident",
+                                          (unsigned long long)i);
+        const cobs_params &A = parts[0]->params, &B = p->params;
+        if (p->device != parts[0]->device) return set_error(COBS_ERR_ARG, "parts on different devices");
+        if (A.term_kind != B.term_kind || A.q != B.q || A.num_hashes != B.num_hashes)
+            return set_error(COBS_ERR_ARG, "parts differ in term kind, q or number of hashes");
+    }
+    CU(cudaSetDevice(parts[0]->device));
+    cobs_device_index *dix = new cobs_device_index();
+    dix->params = parts[0]->params;
+    dix->device = parts[0]->device;
+    std::vector<uintptr_t> addr;  // device address of every block's rows
+    for (uint64_t i = 0; i < n_parts; i++) {
+        const cobs_device_index *p = parts[i];
+        dix->params.score_bits = std::max(dix->params.score_bits, p->params.score_bits);
+        dix->params.block_docs = std::max(dix->params.block_docs, p->params.block_docs);
+        if (p->params.width != dix->params.width) dix->params.width = 0;
+        for (size_t b = 0; b < p->blocks.size(); b++) {
+            cobs_block_info B = p->blocks[b];
+            addr.push_back((uintptr_t)p->dev_rows() + (p->dev_row_offset.empty() ? B.row_offset : p->dev_row_offset[b]));
+            B.row_offset = dix->rows_bytes;
+            B.doc_begin += dix->n_docs;
+            dix->rows_bytes += B.w * B.rowbytes;
+            dix->max_block_bytes = std::max<uint64_t>(dix->max_block_bytes, B.w * B.rowbytes);
+            dix->blocks.push_back(B);
+        }
+        for (uint64_t id : p->perm) dix->perm.push_back(id + dix->n_docs);
+        dix->nterms.insert(dix->nterms.end(), p->nterms.begin(), p->nterms.end());
+        dix->n_docs += p->n_docs;
+    }
+    if (dix->blocks.size() > 1 && dix->params.block_docs == 0) {
+        uint64_t bmax = 0;
+        for (const auto &b : dix->blocks) bmax = std::max(bmax, b.n_docs);
+        dix->params.block_docs = bmax;  // several blocks: no longer one classic block
+    }
+    if (!addr.empty()) {
+        const uintptr_t base = *std::min_element(addr.begin(), addr.end());
+        dix->rows_view = (const uint8_t *)base;
+        for (uintptr_t x : addr) dix->dev_row_offset.push_back((uint64_t)(x - base));
+    }
+    cobs_status st = upload_tables(dix, nullptr);
+    if (st != COBS_OK) {
+        delete dix;
+        return st;
+    }
+    *out = dix;
+    return COBS_OK;
+}
+
 extern "C" void cobs_index_free(cobs_index *ix) { delete ix; }
 extern "C" void cobs_device_index_free(cobs_device_index *dix) {
     if (!dix) return;
@@ -443,13 +509,75 @@ extern "C" cobs_status cobs_device_index_info(const cobs_device_index *dix, cobs
     if (n_docs) *n_docs = dix->n_docs;
     if (n_blocks) *n_blocks = dix->blocks.size();
     if (blocks) *blocks = dix->blocks.data();
-    if (rows_dev) *rows_dev = dix->streamed ? nullptr : dix->rows.p;
+    if (rows_dev) *rows_dev = (dix->streamed || dix->rows_view) ? nullptr : dix->rows.p;
     if (rows_bytes) *rows_bytes = dix->rows_bytes;
     return COBS_OK;
 }
 
+// ------------------------------------------------------------------ merge
+extern "C" cobs_status cobs_index_merge(const cobs_index *a, const cobs_index *b, cobs_index **out) {
+    if (!a || !b || !out) return set_error(COBS_ERR_ARG, "NULL argument");
+    const cobs_params &A = a->params, &B = b->params;
+    if (A.term_kind != B.term_kind || A.q != B.q || A.num_hashes != B.num_hashes)
+        return set_error(COBS_ERR_ARG, "indexes differ in term kind, q or number of hashes");
+    cobs_index *ix = new cobs_index();
+    ix->params = A;
+    ix->params.score_bits = std::max(A.score_bits, B.score_bits);
+    ix->n_docs = a->n_docs + b->n_docs;
+    ix->nterms = a->nterms;
+    ix->nterms.insert(ix->nterms.end(), b->nterms.begin(), b->nterms.end());
+    const bool classic = A.block_docs == 0 && B.block_docs == 0 && a->blocks.size() == 1 && b->blocks.size() == 1 &&
+                         a->blocks[0].w == b->blocks[0].w;
+    if (classic) {
+        // one block: row r = a's bits of row r, then b's bits shifted to column n_a
+        const cobs_block_info &ba = a->blocks[0], &bb = b->blocks[0];
+        cobs_block_info m{};
+        m.n_docs = ix->n_docs;
+        m.doc_begin = 0;
+        m.w = ba.w;
+        m.rowbytes = (m.n_docs + 127) / 128 * 16;
+        m.row_offset = 0;
+        m.max_terms = std::max(ba.max_terms, bb.max_terms);
+        ix->blocks.push_back(m);
+        ix->params.width = m.w;
+        ix->perm.resize(ix->n_docs);
+        std::iota(ix->perm.begin(), ix->perm.end(), 0ULL);
+        ix->rows.assign(m.w * m.rowbytes, 0);
+        const uint64_t na = ba.n_docs, nbytes_a = (na + 7) / 8, nbytes_b = (bb.n_docs + 7) / 8;
+        const uint32_t sh = (uint32_t)(na & 7);
+        for (uint64_t r = 0; r < m.w; r++) {
+            uint8_t *dst = ix->rows.data() + r * m.rowbytes;
+            const uint8_t *ra = a->rows.data() + ba.row_offset + r * ba.rowbytes;
+            const uint8_t *rb = b->rows.data() + bb.row_offset + r * bb.rowbytes;
+            memcpy(dst, ra, nbytes_a);  // padding bits of a's last byte are zero
+            for (uint64_t k = 0; k < nbytes_b; k++) {
+                const uint64_t at = (na >> 3) + k;
+                dst[at] |= (uint8_t)(rb[k] << sh);
+                if (sh && at + 1 < m.rowbytes) dst[at + 1] |= (uint8_t)(rb[k] >> (8 - sh));
+            }
+        }
+    } else {
+        ix->blocks = a->blocks;
+        for (cobs_block_info blk : b->blocks) {
+            blk.row_offset += a->rows.size();
+            blk.doc_begin += a->n_docs;
+            ix->blocks.push_back(blk);
+        }
+        uint64_t bmax = 0;
+        for (const auto &blk : ix->blocks) bmax = std::max(bmax, blk.n_docs);
+        if (ix->blocks.size() > 1 || A.block_docs) ix->params.block_docs = std::max(bmax, std::max(A.block_docs, B.block_docs));
+        if (A.width != B.width) ix->params.width = 0;
+        ix->perm = a->perm;
+        for (uint64_t p : b->perm) ix->perm.push_back(p + a->n_docs);
+        ix->rows = a->rows;
+        ix->rows.insert(ix->rows.end(), b->rows.begin(), b->rows.end());
+    }
+    *out = ix;
+    return COBS_OK;
+}
+
 // ------------------------------------------------------------------ files
-static const char MAGIC[8] = {'C', 'O', 'B', 'S', 'G', 'P', 'U', '1'};
+static const char MAGIC[8] = {'C', 'O', 'B', 'S', 'G', 'P', 'U', '2'};
 
 extern "C" cobs_status cobs_index_save(const cobs_index *ix, const char *path) {
     if (!ix || !path) return set_error(COBS_ERR_ARG, "NULL argument");
@@ -839,7 +967,7 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
             launch_query_terms(ta, 1, s);
             CU(cudaMemsetAsync(eng->scores.p, 0, dix->n_docs * 4, s));
             PlainArgs pa{};
-            pa.rows = dix->rows.as<uint8_t>();
+            pa.rows = dix->dev_rows();
             pa.blocks = dix->dblocks.as<DevBlock>();
             pa.col_block = dix->col_block.as<uint32_t>();
             pa.col_byte = dix->col_byte.as<uint32_t>();
@@ -927,7 +1055,7 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
             }
         };
         if (!dix->streamed) {
-            gather_classes(dix->rows.as<uint8_t>(), 0, eng->n_slices, ctr + 1);  // classes <= 4 < 15
+            gather_classes(dix->dev_rows(), 0, eng->n_slices, ctr + 1);  // classes <= 4 < 15
         } else {
             // Block b: the copy stream fills slot b mod S once every class's gathers
             // of block b - S have read it; each class gathers block b once it is in.

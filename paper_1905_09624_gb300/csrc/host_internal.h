@@ -109,6 +109,12 @@ struct cobs_device_index {
     bool streamed = false;
     cobs::PinBuf host_rows;
     uint64_t max_block_bytes = 0;
+    // multi-index view: rows borrowed from resident parts; block b's rows start at
+    // rows_view + dev_row_offset[b] on the device (blocks[].row_offset stays the
+    // packed offset of the merged layout)
+    const uint8_t *rows_view = nullptr;
+    std::vector<uint64_t> dev_row_offset;
+    const uint8_t *dev_rows() const { return rows_view ? rows_view : rows.as<uint8_t>(); }
 };
 
 struct cobs_engine {

@@ -143,7 +143,7 @@ extern "C" cobs_status cobs_query_one_noalloc(cobs_device_index *dix, const uint
     launch_query_terms(ta, 1, s);
 
     PlainArgs pa{};
-    pa.rows = dix->rows.as<uint8_t>();
+    pa.rows = dix->dev_rows();
     pa.blocks = dix->dblocks.as<DevBlock>();
     pa.col_block = dix->col_block.as<uint32_t>();
     pa.col_byte = dix->col_byte.as<uint32_t>();

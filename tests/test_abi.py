@@ -44,7 +44,7 @@ def test_bloom_width_matches_oracle():
 
 def _write_index_file(path, params, blocks, perm, nterms, rows):
     with open(path, "wb") as f:
-        f.write(b"COBSGPU1")
+        f.write(b"COBSGPU2")
         f.write(bytes(params))
         f.write(struct.pack("<QQQ", len(perm), len(blocks), len(rows)))
         for b in blocks:
@@ -71,7 +71,7 @@ def test_index_file_roundtrip_and_format_errors(tmp_path):
     assert open(p, "rb").read() == open(q, "rb").read()
     # truncated, wrong magic, inconsistent table
     data = open(p, "rb").read()
-    for bad in (data[:-1], b"XOBSGPU1" + data[8:]):
+    for bad in (data[:-1], b"XOBSGPU2" + data[8:]):
         open(p, "wb").write(bad)
         with pytest.raises(cobs.CobsError) as e:
             cobs.HostIndex.load(p)
