@@ -132,7 +132,7 @@ def test_dna_kinds_and_lengths(kind, q):
     assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
 
 
-@pytest.mark.parametrize("q,h", [(8, 3), (5, 2), (3, 1)])
+@pytest.mark.parametrize("q,h", [(8, 3), (5, 2), (3, 1), (6, 4), (8, 5)])
 def test_text_qgrams_multi_hash(q, h):
     wl = synth.config4(n_docs=400, n_q=120, n_words=3000, median=3000, lo=50, hi=20000, block_docs=128)
     wl.q, wl.num_hashes = q, h
@@ -141,6 +141,18 @@ def test_text_qgrams_multi_hash(q, h):
     assert_index_equal(dix, ref)
     for flags in FORMS:
         got = dix.query(wl.queries, wl.q_off, wl.thresholds, flags)
+        assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
+
+
+@pytest.mark.parametrize("slice_bytes", [32, 64, 128])
+def test_multi_hash_slice_widths(slice_bytes):
+    # h = 3: 128-byte slices run the pipelined kernel, narrower ones the register kernel
+    wl = synth.config4(n_docs=300, n_q=80, n_words=2000, median=2500, lo=50, hi=20000, block_docs=128)
+    ref = oracle_index(wl)
+    dix = device_index(wl)
+    eng = cobs.Engine(dix, slice_bytes=slice_bytes)
+    for flags in (cobs.COBS_BATCHED, cobs.COBS_GRAPH):
+        got = eng.query_host(wl.queries, wl.q_off, wl.thresholds, flags)
         assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
 
 
