@@ -811,6 +811,18 @@ static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n
         bp.max_npos = std::max(bp.max_npos, np);
     }
     if (bp.tcap == 0) bp.tcap = TERM_ALIGN;
+    bp.long_q.clear();
+    bp.chunk_q.clear();
+    bp.chunk_w0.clear();
+    const uint64_t round = terms_round_windows();
+    for (uint64_t q = 0; q < n; q++) {
+        if (bp.npos[q] <= round) continue;
+        bp.long_q.push_back((uint32_t)q);
+        for (uint64_t w0 = 0; w0 < bp.npos[q]; w0 += round) {
+            bp.chunk_q.push_back((uint32_t)q);
+            bp.chunk_w0.push_back((uint32_t)w0);
+        }
+    }
     // queries by windows, longest first, ties in input order: a stable LSD radix
     // sort on the complemented window count (below 2^24), two 12-bit digits
     std::vector<uint32_t> order(n);
@@ -877,9 +889,11 @@ static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n
     return COBS_OK;
 }
 
-// Plan upload: term_base[n] | table_base[n] (u64) | items | split queries (uint4).
+// Plan upload: term_base[n] | table_base[n] (u64) | items | split queries (uint4)
+// | long queries | chunk queries | chunk first windows (u32).
 static uint64_t plan_bytes(const BatchPlan &bp) {
-    return bp.n * 16 + bp.items.size() * 16 + bp.split.size() * 16;
+    return bp.n * 16 + bp.items.size() * 16 + bp.split.size() * 16 +
+           (bp.long_q.size() + 2 * bp.chunk_q.size()) * 4;
 }
 
 static cobs_status ensure_buffers(cobs_engine *eng, const BatchPlan &bp) {
@@ -887,6 +901,7 @@ static cobs_status ensure_buffers(cobs_engine *eng, const BatchPlan &bp) {
     const uint64_t nb = eng->dix->blocks.size(), h = eng->dix->params.num_hashes;
     CU(eng->plan.ensure(plan_bytes(bp) + 64));
     CU(eng->partials.ensure(bp.n_parts * eng->dix->n_docs * 2));
+    CU(eng->long_flag.ensure(n * 4));
     CU(eng->ell.ensure(n * 4));
     CU(eng->minsc.ensure(n * 4));
     // qcount, then the counters (one memset clears both): [0] hits, [1..14] work
@@ -930,6 +945,9 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
     const uint64_t *table_base = (const uint64_t *)(plan + n * 8);
     const uint4 *items = (const uint4 *)(plan + n * 16);
     const uint4 *split = items + bp.items.size();
+    const uint32_t *long_q = (const uint32_t *)(split + bp.split.size());
+    const uint32_t *chunk_q = long_q + bp.long_q.size();
+    const uint32_t *chunk_w0 = chunk_q + bp.chunk_q.size();
     unsigned long long *ctr = counters_of(eng, n);
     const uint64_t n_ctr = 16 + (dix->streamed ? 4 * dix->blocks.size() : 0);
     eng->stat_launches = 0;
@@ -1001,6 +1019,20 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
         if (timed) CU(cudaEventRecord(eng->ev[2], s));
     } else {
         ta.q0 = 0;
+        if (!bp.long_q.empty()) {
+            // long queries: sets cleared, distinct counts and flags zeroed, then a
+            // CTA per chunk and a CTA per (query, block group)
+            CU(cudaMemsetAsync(eng->tables.p, 0xFF, bp.total_slots * 8, s));
+            CU(cudaMemsetAsync(eng->ell.p, 0, n * 4, s));
+            CU(cudaMemsetAsync(eng->long_flag.p, 0, n * 4, s));
+            ta.long_q = long_q;
+            ta.chunk_q = chunk_q;
+            ta.chunk_w0 = chunk_w0;
+            ta.long_flag = eng->long_flag.as<uint32_t>();
+            ta.n_long = (uint32_t)bp.long_q.size();
+            ta.n_chunks = (uint32_t)bp.chunk_q.size();
+            eng->stat_launches += 2;
+        }
         launch_query_terms(ta, (uint32_t)n, s);
         eng->stat_launches += 1;
         CU(cudaGetLastError());
@@ -1144,6 +1176,13 @@ static void fill_pinned_plan(cobs_engine *eng) {
     memcpy(p + bp.n * 8, bp.table_base.data(), bp.n * 8);
     if (!bp.items.empty()) memcpy(p + bp.n * 16, bp.items.data(), bp.items.size() * 16);
     if (!bp.split.empty()) memcpy(p + bp.n * 16 + bp.items.size() * 16, bp.split.data(), bp.split.size() * 16);
+    uint8_t *u = p + bp.n * 16 + (bp.items.size() + bp.split.size()) * 16;
+    const size_t nl = bp.long_q.size(), nc = bp.chunk_q.size();
+    if (nl) memcpy(u, bp.long_q.data(), nl * 4);
+    if (nc) {
+        memcpy(u + nl * 4, bp.chunk_q.data(), nc * 4);
+        memcpy(u + (nl + nc) * 4, bp.chunk_w0.data(), nc * 4);
+    }
 }
 
 static std::vector<uint64_t> graph_signature(cobs_engine *eng, const uint8_t *d_bytes, const uint64_t *d_off,
@@ -1160,7 +1199,8 @@ static std::vector<uint64_t> graph_signature(cobs_engine *eng, const uint8_t *d_
                                  (uint64_t)eng->tmp.p, (uint64_t)eng->out_ids.p, (uint64_t)eng->out_scores.p,
                                  (uint64_t)eng->pin_count.p, (uint64_t)eng->slices.p, eng->n_slices,
                                  (uint64_t)bp.items.size(), (uint64_t)bp.split.size(), bp.n_parts,
-                                 (uint64_t)eng->partials.p};
+                                 (uint64_t)eng->partials.p, (uint64_t)bp.long_q.size(), (uint64_t)bp.chunk_q.size(),
+                                 (uint64_t)eng->long_flag.p};
     for (const auto &c : bp.classes) {
         sig.push_back(c.begin);
         sig.push_back(c.count);

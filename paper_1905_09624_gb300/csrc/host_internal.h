@@ -80,6 +80,9 @@ struct BatchPlan {
     std::vector<Item> items;        // work items of the batched kernel
     std::vector<Item> split;        // split queries: (query, first slot, slots, 0)
     uint64_t n_parts = 0;           // partial slots
+    // long queries (more windows than one round of the term kernel): one term
+    // CTA per round (chunk), then one row CTA per (query, block group)
+    std::vector<uint32_t> long_q, chunk_q, chunk_w0;
     uint64_t tcap = 0, total_slots = 0, sum_npos = 0, max_npos = 0;
     uint32_t smem_slots = 16;  // largest distinct set of the batch kept in shared memory
 };
@@ -132,6 +135,7 @@ struct cobs_engine {
     cobs::DevBuf qbytes, qoff, thr;          // staging of host queries
     cobs::DevBuf plan;                        // term_base | table_base | items | split
     cobs::DevBuf partials;                    // split items: counts per (slot, document)
+    cobs::DevBuf long_flag;                   // per query: EMPTY_KEY code seen (long queries)
     cobs::DevBuf ell, minsc, qcount, qcursor, hitoff, biglist;
     cobs::DevBuf counters;                    // [0] hit count, [1..] work counters
     cobs::DevBuf rows_idx, tables, codes;

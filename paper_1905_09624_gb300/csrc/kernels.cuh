@@ -29,8 +29,18 @@ struct TermsArgs {
     uint32_t n_blocks, h, kind, k;
     uint32_t q0;                   // first query handled by blockIdx.x == 0
     uint32_t smem_slots;           // sets of up to this many slots live in shared memory (<= TERMS_SMEM_SLOTS)
+    // Chunk plan of the long queries (more windows than one round): with
+    // n_chunks > 0 every long query is processed by one CTA per round (its set
+    // at tables + table_base[q] filled with EMPTY_KEY, ell[q] and long_flag[q]
+    // zero before the launch), then one CTA per (query, group of blocks).
+    const uint32_t *long_q;        // n_long long queries
+    const uint32_t *chunk_q;       // per chunk: query
+    const uint32_t *chunk_w0;      // per chunk: first window (a multiple of the round)
+    uint32_t *long_flag;           // per query: the EMPTY_KEY code was seen
+    uint32_t n_long, n_chunks;
 };
 void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s);
+uint32_t terms_round_windows();    // windows per round (long queries have more)
 
 // Batched gather/AND/ADD with fused threshold (persistent).
 struct SliceDesc {

@@ -1,9 +1,9 @@
-// K1: query terms.  For every query (one CTA each): all windows of length q
-// (Sec. 2.1), canonical form (Sec. 2.3), the distinct set G_q(P) via an
-// open-addressing set, then for every distinct term and every block b and hash
-// i < h its row XXH64(term, i) mod w_b (Sec. 2.2), written as a u32 row index.
+// K1: query terms.  For every query: all windows of length q (Sec. 2.1),
+// canonical form (Sec. 2.3), the distinct set G_q(P) via an open-addressing set,
+// then for every distinct term and every block b and hash i < h its row
+// XXH64(term, i) mod w_b (Sec. 2.2), written as a u32 row index.
 //
-// The query is processed in rounds of TERMS_ROUND windows.  For DNA each round
+// A query is processed in rounds of TERMS_ROUND windows.  For DNA each round
 // packs its bytes straight from global memory into a 2-bit base stream and a
 // mask of non-ACGT bytes, 16 bases per word (every thread packs 4 bytes, four
 // lanes merge a word); byte q-grams stage the bytes in shared memory.  Every
@@ -12,11 +12,20 @@
 // bit reversal of the complemented code with the bits of each base swapped back.
 // The window is hashed, inserted into the set and appended to the distinct list
 // when it is new (warp-aggregated).  A final pass writes the rows in row-bucket
-// order.  With one hash and at most two blocks the rows of a new term are
-// computed at insertion: the list holds them (block 1 in the high word) and the
-// bucket histogram is counted on the way, so the final pass only scatters.
-// Otherwise the list holds hash 0 when h == 1, else the code, and the final pass
+// order.
+//
+// Short queries (one round) run fused in one CTA with the set in shared memory.
+// With one hash and at most two blocks the rows of a new term are computed at
+// insertion: the list holds them (block 1 in the high word) and the bucket
+// histogram is counted on the way, so the final pass only scatters.  Otherwise
+// the list holds hash 0 when h == 1, else the code, and the final pass
 // recomputes the rows.
+//
+// Long queries, when the caller supplies a chunk plan, are spread over many
+// CTAs: one CTA per round inserts into the query's set in global memory
+// (cleared by the caller) and appends to its global list, counting the
+// distinct terms with a global atomic; then one CTA per (query, group of
+// blocks) runs the row pass.  Without a chunk plan one CTA walks all rounds.
 #include "kernels.cuh"
 
 namespace cobs {
@@ -26,6 +35,195 @@ constexpr uint32_t TERMS_STAGE_BYTES = TERMS_ROUND + 32;      // + k - 1 <= 31 b
 // packed words of a round: data words + 2 read past the last window, rounded up
 // so the packing loop runs whole warps (4 bytes per lane, 8 words per warp)
 constexpr uint32_t TERMS_PK_WORDS = (((TERMS_STAGE_BYTES + 15) / 16 + 2) * 4 + 31) / 32 * 8;
+constexpr uint32_t BP = TERMS_BLOCKS_PER_PASS;
+
+// Bytes of windows [r0, r0 + rn) of a query into shared memory: DNA as packed
+// bases and a mask of non-ACGT bytes, bytes as they are.  Every thread of the
+// CTA calls it; the caller synchronises before (buffers free) and after.
+__device__ __forceinline__ void stage_round(const uint8_t *src, uint64_t r0, uint32_t rn, uint32_t k, bool dna,
+                                            uint8_t *s_bytes, uint32_t *s_pk, uint16_t *s_inv) {
+    const uint32_t nbytes = rn + k - 1;
+    if (dna) {
+        // 4 bytes per lane -> 8 bits of bases and 4 mask bits; lanes 4j..4j+3 form word j
+        const uint32_t nquads = (((nbytes + 15) / 16 + 2) * 4 + 31) & ~31u;
+        for (uint32_t t = threadIdx.x; t < nquads; t += blockDim.x) {
+            uint32_t pk = 0, inv = 0;
+#pragma unroll
+            for (uint32_t j = 0; j < 4; j++) {
+                const uint32_t i = 4 * t + j;
+                const uint32_t c = i < nbytes ? src[r0 + i] : 0u;
+                const bool ok = c == 'A' || c == 'C' || c == 'G' || c == 'T';
+                uint32_t b = (c >> 1) & 3u;  // A, C, T, G -> 0, 1, 2, 3
+                b ^= b >> 1;                 // -> A 0, C 1, G 2, T 3
+                pk = (pk << 2) | (ok ? b : 0u);
+                inv = (inv << 1) | (ok ? 0u : 1u);
+            }
+            const uint32_t sub = 3u - (t & 3u);  // first quad of a word is most significant
+            pk <<= 8 * sub;
+            inv <<= 4 * sub;
+            pk |= __shfl_xor_sync(0xffffffffu, pk, 1);
+            inv |= __shfl_xor_sync(0xffffffffu, inv, 1);
+            pk |= __shfl_xor_sync(0xffffffffu, pk, 2);
+            inv |= __shfl_xor_sync(0xffffffffu, inv, 2);
+            if ((t & 3u) == 0u) {
+                s_pk[t >> 2] = pk;
+                s_inv[t >> 2] = (uint16_t)inv;
+            }
+        }
+    } else {
+        for (uint32_t i = threadIdx.x; i < nbytes; i += blockDim.x) s_bytes[i] = src[r0 + i];
+    }
+}
+
+// Shared-memory helpers of the rows-at-insertion path (h == 1, at most two blocks).
+struct FastRows {
+    bool on;
+    uint32_t nb;
+    const uint64_t *m;   // Barrett constants
+    const uint32_t *w;   // row counts
+    const uint32_t *shift;
+    uint32_t *hist;      // 2 x TERMS_BUCKETS
+};
+
+// Windows [0, rn) of a staged round: extract, hash, insert into `table` (cap
+// slots) and append each new term to `list` at a slot counted by *ell_ctr
+// (shared or global; one atomic per warp and iteration).  *has_empty flags the
+// one code the set cannot hold.
+__device__ __forceinline__ void insert_round(const TermsArgs &a, uint32_t rn, uint32_t k, uint64_t mask, bool dna,
+                                             const uint8_t *s_bytes, const uint32_t *s_pk, const uint16_t *s_inv,
+                                             unsigned long long *table, uint32_t cap, unsigned long long *list,
+                                             uint32_t *ell_ctr, uint32_t *has_empty, const FastRows &fr) {
+    const uint32_t lane = threadIdx.x & 31u;
+    // one window per thread and iteration; every lane of a warp runs the same
+    // number of iterations, for the warp-level append
+    for (uint32_t p = threadIdx.x; p < ((rn + 31u) & ~31u); p += blockDim.x) {
+        uint64_t code = 0;
+        bool term = false;
+        if (p < rn) {
+            if (dna) {
+                term = packed_kmer(s_pk, s_inv, p, k, a.kind == KIND_DNA_CANONICAL, mask, &code);
+            } else {
+                code = bytes_qgram(s_bytes, p, k);
+                term = true;
+            }
+        }
+        bool fresh = false;
+        uint64_t h0 = 0;
+        if (term) {
+            h0 = xxh64_u64(code, 0);
+            if (code == EMPTY_KEY) fresh = atomicExch(has_empty, 1u) == 0u;
+            else fresh = set_insert(table, cap, h0, code);
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, fresh);
+        if (m) {
+            uint32_t slot0 = 0;
+            const uint32_t leader = __ffs(m) - 1;
+            if (lane == leader) slot0 = atomicAdd(ell_ctr, (uint32_t)__popc(m));
+            slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+            if (fresh) {
+                uint64_t entry = a.h == 1 ? h0 : code;
+                if (fr.on) {
+                    const uint32_t rw0 = barrett_mod(h0, fr.m[0], fr.w[0]);
+                    atomicAdd(&fr.hist[rw0 >> fr.shift[0]], 1u);
+                    uint32_t rw1 = 0;
+                    if (fr.nb > 1) {
+                        rw1 = barrett_mod(h0, fr.m[1], fr.w[1]);
+                        atomicAdd(&fr.hist[TERMS_BUCKETS + (rw1 >> fr.shift[1])], 1u);
+                    }
+                    entry = ((uint64_t)rw1 << 32) | rw0;
+                }
+                list[slot0 + __popc(m & ((1u << lane) - 1u))] = entry;
+            }
+        }
+    }
+}
+
+// Exclusive scan of the 64 bucket counts at hj, by one warp.
+__device__ __forceinline__ void scan_hist(uint32_t *hj) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t carry = 0;
+    for (uint32_t c0 = 0; c0 < TERMS_BUCKETS; c0 += 32) {
+        const uint32_t v = hj[c0 + lane];
+        uint32_t x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if ((int)lane >= d) x += y;
+        }
+        hj[c0 + lane] = carry + x - v;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+}
+
+// Row pass for blocks [b0, b0 + nbp), nbp <= BP: the distinct terms' rows in
+// row-bucket order (a counting sort by the top bits of the hash-0 row).  Scores
+// do not depend on the order of the terms; bucketed order makes all warps of
+// the gather sweep the rows of a slice together, so the rows in use at any
+// moment form a narrow band.  list[t] is hash 0 (h == 1) or the code.  Every
+// thread of the CTA calls it.
+__device__ __forceinline__ void row_pass(const TermsArgs &a, const unsigned long long *list, uint32_t ell,
+                                         uint64_t base, uint32_t b0, uint32_t nbp, uint32_t *s_hist,
+                                         uint32_t *s_shift) {
+    const uint32_t warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    // every distinct term once, spread over the threads: f(code, hash 0); the code
+    // is only meaningful (and only used) when h > 1
+    auto each_distinct = [&](auto &&f) {
+        for (uint32_t t = threadIdx.x; t < ell; t += blockDim.x) {
+            const uint64_t key = list[t];
+            f(key, a.h == 1 ? key : xxh64_u64(key, 0));
+        }
+    };
+    for (uint32_t i = threadIdx.x; i < nbp * TERMS_BUCKETS; i += blockDim.x) s_hist[i] = 0;
+    if (threadIdx.x < nbp) {
+        const uint32_t w = a.blocks[b0 + threadIdx.x].w;
+        const int lg = 32 - __clz(w > 1 ? w - 1 : 0);  // bits of the largest row
+        s_shift[threadIdx.x] = lg > (int)TERMS_BUCKET_BITS ? (uint32_t)(lg - TERMS_BUCKET_BITS) : 0u;
+    }
+    __syncthreads();
+    each_distinct([&](uint64_t, uint64_t h0) {
+#pragma unroll
+        for (uint32_t j = 0; j < BP; j++) {
+            if (j < nbp) {
+                const DevBlock blk = a.blocks[b0 + j];
+                const uint32_t r0 = barrett_mod(h0, blk.barrett_m, blk.w);
+                atomicAdd(&s_hist[j * TERMS_BUCKETS + (r0 >> s_shift[j])], 1u);
+            }
+        }
+    });
+    __syncthreads();
+    for (uint32_t j = warp; j < nbp; j += n_warps) scan_hist(s_hist + j * TERMS_BUCKETS);
+    __syncthreads();
+    each_distinct([&](uint64_t code, uint64_t h0) {
+        uint32_t pos[BP];
+#pragma unroll
+        for (uint32_t j = 0; j < BP; j++) {
+            if (j < nbp) {
+                const DevBlock blk = a.blocks[b0 + j];
+                const uint32_t r0 = barrett_mod(h0, blk.barrett_m, blk.w);
+                pos[j] = atomicAdd(&s_hist[j * TERMS_BUCKETS + (r0 >> s_shift[j])], 1u);
+                a.rows_idx[(uint64_t)((b0 + j) * a.h) * a.tcap + base + pos[j]] = r0;
+            }
+        }
+        for (uint32_t i2 = 1; i2 < a.h; i2++) {
+            const uint64_t hv = xxh64_u64(code, i2);
+#pragma unroll
+            for (uint32_t j = 0; j < BP; j++) {
+                if (j < nbp) {
+                    const DevBlock blk = a.blocks[b0 + j];
+                    a.rows_idx[(uint64_t)((b0 + j) * a.h + i2) * a.tcap + base + pos[j]] =
+                        barrett_mod(hv, blk.barrett_m, blk.w);
+                }
+            }
+        }
+    });
+    __syncthreads();
+}
+
+__device__ __forceinline__ uint64_t windows_of(const TermsArgs &a, uint32_t q, uint64_t *off0) {
+    *off0 = a.offsets[q];
+    const uint64_t len = a.offsets[q + 1] - *off0;
+    return len >= a.k ? len - a.k + 1 : 0;
+}
 
 __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     extern __shared__ unsigned long long s_table[];
@@ -35,15 +233,14 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     __shared__ uint16_t s_inv[TERMS_PK_WORDS];  // non-ACGT bytes, 16 per word
     __shared__ uint32_t s_ell;
     __shared__ uint32_t s_has_empty;
-    constexpr uint32_t BP = TERMS_BLOCKS_PER_PASS;
     __shared__ uint32_t s_hist[BP * TERMS_BUCKETS];
     __shared__ uint32_t s_shift[BP];
 
     const uint32_t q = a.q0 + blockIdx.x;
-    const uint64_t off0 = a.offsets[q];
-    const uint64_t len = a.offsets[q + 1] - off0;
+    uint64_t off0;
+    const uint64_t npos = windows_of(a, q, &off0);
+    if (a.n_chunks && npos > TERMS_ROUND) return;  // a long query of the chunk plan
     const uint32_t k = a.k;
-    const uint64_t npos = len >= k ? len - k + 1 : 0;
     const uint32_t cap = (uint32_t)set_slots(npos);
     // a set that fits on chip holds at most TERMS_ROUND distinct terms (one round)
     const bool in_smem = cap <= a.smem_slots;
@@ -68,110 +265,23 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     }
     if (rows_in_list)
         for (uint32_t i = threadIdx.x; i < 2 * TERMS_BUCKETS; i += blockDim.x) s_hist[i] = 0;
+    const FastRows fr{rows_in_list, nb_fast, s_fm, s_fw, s_shift, s_hist};
 
     const uint8_t *src = a.bytes + off0;
     const uint64_t mask = kmer_mask(k);
-    const uint32_t lane = threadIdx.x & 31u;
-
     const bool dna = a.kind != KIND_BYTES;
     for (uint64_t r0 = 0; r0 < npos; r0 += TERMS_ROUND) {
         const uint32_t rn = (uint32_t)(npos - r0 < TERMS_ROUND ? npos - r0 : TERMS_ROUND);
-        const uint32_t nbytes = rn + k - 1;
         __syncthreads();  // previous round finished with the staged bases (and the table init)
-        if (dna) {
-            // 4 bytes per lane -> 8 bits of bases and 4 mask bits; lanes 4j..4j+3 form word j
-            const uint32_t nquads = (((nbytes + 15) / 16 + 2) * 4 + 31) & ~31u;
-            for (uint32_t t = threadIdx.x; t < nquads; t += blockDim.x) {
-                uint32_t pk = 0, inv = 0;
-#pragma unroll
-                for (uint32_t j = 0; j < 4; j++) {
-                    const uint32_t i = 4 * t + j;
-                    const uint32_t c = i < nbytes ? src[r0 + i] : 0u;
-                    const bool ok = c == 'A' || c == 'C' || c == 'G' || c == 'T';
-                    uint32_t b = (c >> 1) & 3u;  // A, C, T, G -> 0, 1, 2, 3
-                    b ^= b >> 1;                 // -> A 0, C 1, G 2, T 3
-                    pk = (pk << 2) | (ok ? b : 0u);
-                    inv = (inv << 1) | (ok ? 0u : 1u);
-                }
-                const uint32_t sub = 3u - (t & 3u);  // first quad of a word is most significant
-                pk <<= 8 * sub;
-                inv <<= 4 * sub;
-                pk |= __shfl_xor_sync(0xffffffffu, pk, 1);
-                inv |= __shfl_xor_sync(0xffffffffu, inv, 1);
-                pk |= __shfl_xor_sync(0xffffffffu, pk, 2);
-                inv |= __shfl_xor_sync(0xffffffffu, inv, 2);
-                if ((t & 3u) == 0u) {
-                    s_pk[t >> 2] = pk;
-                    s_inv[t >> 2] = (uint16_t)inv;
-                }
-            }
-        } else {
-            for (uint32_t i = threadIdx.x; i < nbytes; i += blockDim.x) s_bytes[i] = src[r0 + i];
-        }
+        stage_round(src, r0, rn, k, dna, s_bytes, s_pk, s_inv);
         __syncthreads();
-        // one window per thread and iteration; every lane of a warp runs the same
-        // number of iterations, for the warp-level append
-        for (uint32_t p = threadIdx.x; p < ((rn + 31u) & ~31u); p += blockDim.x) {
-            uint64_t code = 0;
-            bool term = false;
-            if (p < rn) {
-                if (dna) {
-                    term = packed_kmer(s_pk, s_inv, p, k, a.kind == KIND_DNA_CANONICAL, mask, &code);
-                } else {
-                    code = bytes_qgram(s_bytes, p, k);
-                    term = true;
-                }
-            }
-            bool fresh = false;
-            uint64_t h0 = 0;
-            if (term) {
-                h0 = xxh64_u64(code, 0);
-                if (code == EMPTY_KEY) fresh = atomicExch(&s_has_empty, 1u) == 0u;
-                else fresh = set_insert(table, cap, h0, code);
-            }
-            const uint32_t m = __ballot_sync(0xffffffffu, fresh);
-            if (m) {
-                uint32_t slot0 = 0;
-                const uint32_t leader = __ffs(m) - 1;
-                if (lane == leader) slot0 = atomicAdd(&s_ell, (uint32_t)__popc(m));
-                slot0 = __shfl_sync(0xffffffffu, slot0, leader);
-                if (fresh) {
-                    uint64_t entry = a.h == 1 ? h0 : code;
-                    if (rows_in_list) {
-                        const uint32_t rw0 = barrett_mod(h0, s_fm[0], s_fw[0]);
-                        atomicAdd(&s_hist[rw0 >> s_shift[0]], 1u);
-                        uint32_t rw1 = 0;
-                        if (nb_fast > 1) {
-                            rw1 = barrett_mod(h0, s_fm[1], s_fw[1]);
-                            atomicAdd(&s_hist[TERMS_BUCKETS + (rw1 >> s_shift[1])], 1u);
-                        }
-                        entry = ((uint64_t)rw1 << 32) | rw0;
-                    }
-                    list[slot0 + __popc(m & ((1u << lane) - 1u))] = entry;
-                }
-            }
-        }
+        insert_round(a, rn, k, mask, dna, s_bytes, s_pk, s_inv, table, cap, list, &s_ell, &s_has_empty, fr);
     }
     __syncthreads();
     const uint32_t ell = s_ell;
     if (threadIdx.x == 0) a.ell[q] = ell;
-    const uint32_t warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
-    // exclusive scan of the 64 bucket counts of block j, by one warp
-    auto scan_hist = [&](uint32_t *hj) {
-        uint32_t carry = 0;
-        for (uint32_t c0 = 0; c0 < TERMS_BUCKETS; c0 += 32) {
-            const uint32_t v = hj[c0 + lane];
-            uint32_t x = v;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-                if ((int)lane >= d) x += y;
-            }
-            hj[c0 + lane] = carry + x - v;
-            carry += __shfl_sync(0xffffffffu, x, 31);
-        }
-    };
     if (rows_in_list) {
+        const uint32_t warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
         for (uint32_t j = warp; j < nb_fast; j += n_warps) scan_hist(s_hist + j * TERMS_BUCKETS);
         __syncthreads();
         for (uint32_t t = threadIdx.x; t < ell; t += blockDim.x) {
@@ -187,68 +297,40 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
         }
         return;
     }
-    // every distinct term once, spread over the threads: f(code, hash 0); the code
-    // is only meaningful (and only used) when h > 1
-    auto each_distinct = [&](auto &&f) {
-        for (uint32_t t = threadIdx.x; t < ell; t += blockDim.x) {
-            const uint64_t key = list[t];
-            f(key, a.h == 1 ? key : xxh64_u64(key, 0));
-        }
-    };
+    // Blocks are handled BP at a time, so every term is hashed once per pass
+    // whatever the number of blocks.
+    for (uint32_t b0 = 0; b0 < a.n_blocks; b0 += BP)
+        row_pass(a, list, ell, base, b0, a.n_blocks - b0 < BP ? a.n_blocks - b0 : BP, s_hist, s_shift);
+}
 
-    // Row pass: per block, the distinct terms' rows in row-bucket order (a counting
-    // sort by the top bits of the hash-0 row).  Scores do not depend on the order
-    // of the terms; bucketed order makes all warps of the gather sweep the rows of
-    // a slice together, so the rows in use at any moment form a narrow band.
-    // Blocks are handled TERMS_BLOCKS_PER_PASS at a time, so every term is hashed
-    // once per pass whatever the number of blocks.
-    for (uint32_t b0 = 0; b0 < a.n_blocks; b0 += BP) {
-        const uint32_t nbp = a.n_blocks - b0 < BP ? a.n_blocks - b0 : BP;
-        for (uint32_t i = threadIdx.x; i < nbp * TERMS_BUCKETS; i += blockDim.x) s_hist[i] = 0;
-        if (threadIdx.x < nbp) {
-            const uint32_t w = a.blocks[b0 + threadIdx.x].w;
-            const int lg = 32 - __clz(w > 1 ? w - 1 : 0);  // bits of the largest row
-            s_shift[threadIdx.x] = lg > (int)TERMS_BUCKET_BITS ? (uint32_t)(lg - TERMS_BUCKET_BITS) : 0u;
-        }
-        __syncthreads();
-        each_distinct([&](uint64_t, uint64_t h0) {
-#pragma unroll
-            for (uint32_t j = 0; j < BP; j++) {
-                if (j < nbp) {
-                    const DevBlock blk = a.blocks[b0 + j];
-                    const uint32_t r0 = barrett_mod(h0, blk.barrett_m, blk.w);
-                    atomicAdd(&s_hist[j * TERMS_BUCKETS + (r0 >> s_shift[j])], 1u);
-                }
-            }
-        });
-        __syncthreads();
-        for (uint32_t j = warp; j < nbp; j += n_warps) scan_hist(s_hist + j * TERMS_BUCKETS);
-        __syncthreads();
-        each_distinct([&](uint64_t code, uint64_t h0) {
-            uint32_t pos[BP];
-#pragma unroll
-            for (uint32_t j = 0; j < BP; j++) {
-                if (j < nbp) {
-                    const DevBlock blk = a.blocks[b0 + j];
-                    const uint32_t r0 = barrett_mod(h0, blk.barrett_m, blk.w);
-                    pos[j] = atomicAdd(&s_hist[j * TERMS_BUCKETS + (r0 >> s_shift[j])], 1u);
-                    a.rows_idx[(uint64_t)((b0 + j) * a.h) * a.tcap + base + pos[j]] = r0;
-                }
-            }
-            for (uint32_t i2 = 1; i2 < a.h; i2++) {
-                const uint64_t hv = xxh64_u64(code, i2);
-#pragma unroll
-                for (uint32_t j = 0; j < BP; j++) {
-                    if (j < nbp) {
-                        const DevBlock blk = a.blocks[b0 + j];
-                        a.rows_idx[(uint64_t)((b0 + j) * a.h + i2) * a.tcap + base + pos[j]] =
-                            barrett_mod(hv, blk.barrett_m, blk.w);
-                    }
-                }
-            }
-        });
-        __syncthreads();
-    }
+// Long queries, insertion: one CTA per round (chunk) of a long query.  The
+// query's set and distinct count start cleared; the list is the query's global
+// term region.
+__global__ void __launch_bounds__(TERMS_THREADS) k_terms_long_insert(TermsArgs a) {
+    __shared__ __align__(16) uint8_t s_bytes[TERMS_STAGE_BYTES];
+    __shared__ uint32_t s_pk[TERMS_PK_WORDS];
+    __shared__ uint16_t s_inv[TERMS_PK_WORDS];
+    const uint32_t q = a.chunk_q[blockIdx.x];
+    const uint64_t r0 = a.chunk_w0[blockIdx.x];
+    uint64_t off0;
+    const uint64_t npos = windows_of(a, q, &off0);
+    const uint32_t rn = (uint32_t)(npos - r0 < TERMS_ROUND ? npos - r0 : TERMS_ROUND);
+    const uint32_t cap = (uint32_t)set_slots(npos);
+    stage_round(a.bytes + off0, r0, rn, a.k, a.kind != KIND_BYTES, s_bytes, s_pk, s_inv);
+    __syncthreads();
+    const FastRows fr{false, 0u, nullptr, nullptr, nullptr, nullptr};
+    insert_round(a, rn, a.k, kmer_mask(a.k), a.kind != KIND_BYTES, s_bytes, s_pk, s_inv,
+                 a.tables + a.table_base[q], cap, a.codes + a.term_base[q], &a.ell[q], &a.long_flag[q], fr);
+}
+
+// Long queries, rows: one CTA per (long query, group of BP blocks).
+__global__ void __launch_bounds__(TERMS_THREADS) k_terms_long_rows(TermsArgs a) {
+    __shared__ uint32_t s_hist[BP * TERMS_BUCKETS];
+    __shared__ uint32_t s_shift[BP];
+    const uint32_t q = a.long_q[blockIdx.x];
+    const uint32_t b0 = blockIdx.y * BP;
+    const uint64_t base = a.term_base[q];
+    row_pass(a, a.codes + base, a.ell[q], base, b0, a.n_blocks - b0 < BP ? a.n_blocks - b0 : BP, s_hist, s_shift);
 }
 
 void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s) {
@@ -262,6 +344,13 @@ void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s) 
     // shared memory sized to the largest set of the launch that is kept on chip
     const size_t dyn = (size_t)a.smem_slots * sizeof(unsigned long long);
     k_query_terms<<<n_queries, TERMS_THREADS, dyn, s>>>(a);
+    if (a.n_chunks) {
+        k_terms_long_insert<<<a.n_chunks, TERMS_THREADS, 0, s>>>(a);
+        const uint32_t groups = (a.n_blocks + BP - 1) / BP;
+        if (groups) k_terms_long_rows<<<dim3(a.n_long, groups), TERMS_THREADS, 0, s>>>(a);
+    }
 }
+
+uint32_t terms_round_windows() { return TERMS_ROUND; }
 
 }  // namespace cobs

@@ -248,3 +248,34 @@ def test_split_long_queries_small_batch():
     for i in range(3, 20):
         if src[i] >= 0 and thr[i] <= 700:
             assert src[i] in got[i][2].tolist()
+
+
+def test_all_ones_qgram_short_and_long_queries():
+    # The 8-byte q-gram of 0xFF bytes is the one code an open-addressing set
+    # cannot hold; it is counted once per query, in short queries (set on chip)
+    # and in long ones (one CTA per 2,048-window chunk), as the oracle does.
+    rng = np.random.default_rng(11)
+    docs = []
+    for d in range(40):
+        b = rng.integers(0, 256, 4000, dtype=np.uint8)
+        if d % 3 == 0:
+            b[500:540] = 0xFF
+        docs.append(b.tobytes())
+    off = np.zeros(len(docs) + 1, np.uint64)
+    off[1:] = np.cumsum([len(x) for x in docs])
+    db = np.frombuffer(b"".join(docs), np.uint8)
+    qs = [docs[0][300:900], docs[3][100:3900] + b"\xff" * 30 + docs[6][0:3000], b"\xff" * 3000, b"\xff" * 9,
+          docs[9][480:560], docs[1][0:2055], docs[2][0:2056] + b"\xff" * 8]
+    qo = np.zeros(len(qs) + 1, np.uint64)
+    qo[1:] = np.cumsum([len(x) for x in qs])
+    qb = np.frombuffer(b"".join(qs), np.uint8)
+    thr = np.array([500, 300, 1000, 1000, 700, 900, 800], np.uint16)
+    for h in (1, 3):
+        wl = synth.Workload("ones", 2, 8, h, 0.3, 16, 32, db, off, qb, qo, thr, np.full(len(qs), -1))
+        ref = oracle_index(wl)
+        dix = device_index(wl)
+        assert_index_equal(dix, ref)
+        for flags in FORMS:
+            got = dix.query(qb, qo, thr, flags)
+            assert_results_equal(got, ref, qs, thr)
+            assert got[2][0] == 1 and got[3][0] == 1  # one distinct term each
