@@ -221,9 +221,10 @@ typedef struct cobs_engine_cfg {
                                  4 = index rows evict-last */
     uint32_t split;           /* long-query split of the batched form (single-hash indexes):
                                  0 = auto (batches too small to give every resident warp
-                                 several tiles split queries of more than 4080 windows
-                                 into parts of 4080 terms, summed before the threshold),
-                                 1 = never, 2 = always */
+                                 several tiles split their long queries into parts of
+                                 256..4080 terms, sized so the tiles cover the resident
+                                 warps about twice; the parts' counts are summed before
+                                 the threshold), 1 = never, 2 = always */
     uint64_t stage_bytes;     /* streamed index only: device bytes of the staging ring, split
                                  into slots of the largest block's bytes (0 = two slots;
                                  at least one slot, at most one per block) */
@@ -266,6 +267,8 @@ typedef struct cobs_query_stats {
     uint32_t split_queries;   /* queries of the last batch that ran as split parts */
     double ms_host;           /* host time of the last query call: planning and enqueueing */
     uint64_t h2d_index_bytes; /* streamed index: row bytes copied to the staging ring */
+    uint32_t split_part;      /* terms per part of the split queries (0: none split) */
+    uint32_t _pad2;
 } cobs_query_stats;
 cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out);
 

@@ -842,29 +842,41 @@ static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n
         }
     }
     // Work items.  A batch too small to give every resident warp several tiles
-    // splits its long queries into items of SPLIT_TERMS terms (h == 1 only), so
-    // one long query no longer runs on a single warp per slice.
+    // splits its long queries into parts (h == 1 only), so one long query no
+    // longer runs on a single warp per slice.  The part size aims at about two
+    // tiles per resident warp: the batch's windows over the items that many
+    // tiles hold, a multiple of TERM_ALIGN between SPLIT_MIN_TERMS and
+    // SPLIT_TERMS.
     const uint64_t qpw = 32 / eng->lanes_per_query;
     const uint64_t warps = (uint64_t)eng->n_sm * eng->ctas_per_sm * 2;
     const bool small = (uint64_t)eng->n_slices * ((n + qpw - 1) / qpw) < 4 * warps;
     bool split = batched && P.num_hashes == 1 && eng->cfg.split != 1 && (eng->cfg.split == 2 || small);
-    if (split) {  // partial counts (2 bytes per part and document) stay below 1 GiB
+    uint64_t part = SPLIT_TERMS;
+    if (split) {
+        const uint64_t items_target = std::max<uint64_t>(1, 2 * warps * qpw / std::max<uint32_t>(eng->n_slices, 1));
+        part = (bp.sum_npos + items_target - 1) / items_target;
+        part = (part + TERM_ALIGN - 1) / TERM_ALIGN * TERM_ALIGN;
+        part = std::min<uint64_t>(std::max<uint64_t>(part, SPLIT_MIN_TERMS), SPLIT_TERMS);
+        // partial counts (2 bytes per part and document) stay below 1 GiB
         uint64_t parts = 0;
         for (uint64_t q = 0; q < n; q++)
-            if (bp.npos[q] > SPLIT_TERMS) parts += (bp.npos[q] + SPLIT_TERMS - 1) / SPLIT_TERMS;
+            if (bp.npos[q] > part) parts += (bp.npos[q] + part - 1) / part;
         split = parts * eng->dix->n_docs * 2 <= (1ULL << 30);
     }
     bp.items.clear();
     bp.split.clear();
     bp.n_parts = 0;
+    bp.part_terms = 0;
     for (uint32_t i = 0; i < n; i++) {
         const uint32_t q = order[i];
         const uint64_t np = bp.npos[q];
-        if (split && np > SPLIT_TERMS) {
-            const uint32_t parts = (uint32_t)((np + SPLIT_TERMS - 1) / SPLIT_TERMS);
+        if (split && np > part) {
+            const uint32_t parts = (uint32_t)((np + part - 1) / part);
+            const uint32_t ps = (uint32_t)part;
+            bp.part_terms = ps;
             bp.split.push_back({q, (uint32_t)bp.n_parts, parts, 0u});
             for (uint32_t p = 0; p < parts; p++)
-                bp.items.push_back({q, p * SPLIT_TERMS, (p + 1) * SPLIT_TERMS, (uint32_t)(bp.n_parts + p)});
+                bp.items.push_back({q, p * ps, (p + 1) * ps, (uint32_t)(bp.n_parts + p)});
             bp.n_parts += parts;
         } else {
             bp.items.push_back({q, 0u, ITEM_WHOLE, ITEM_WHOLE});
@@ -1457,6 +1469,7 @@ extern "C" cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out
     out->split_queries = (uint32_t)eng->bp.split.size();
     out->ms_host = eng->stat_host_ms;
     out->h2d_index_bytes = eng->stat_h2d_index_bytes;
+    out->split_part = eng->bp.part_terms;
     return COBS_OK;
 }
 

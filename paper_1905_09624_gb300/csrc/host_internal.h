@@ -80,6 +80,7 @@ struct BatchPlan {
     std::vector<Item> items;        // work items of the batched kernel
     std::vector<Item> split;        // split queries: (query, first slot, slots, 0)
     uint64_t n_parts = 0;           // partial slots
+    uint32_t part_terms = 0;        // terms per part of the split queries
     // long queries (more windows than one round of the term kernel): one term
     // CTA per round (chunk), then one row CTA per (query, block group)
     std::vector<uint32_t> long_q, chunk_q, chunk_w0;

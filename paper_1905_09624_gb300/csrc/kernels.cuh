@@ -80,6 +80,7 @@ constexpr uint32_t ITEM_WHOLE = 0xFFFFFFFFu;
 // Long queries of small batches are split into items of SPLIT_TERMS terms (a
 // multiple of TERM_ALIGN below 2^12, so a part counts in 12 bit-sliced levels).
 constexpr uint32_t SPLIT_TERMS = 4080;
+constexpr uint32_t SPLIT_MIN_TERMS = 256;   // smallest part of the adaptive split
 
 // Split queries: sum the partial counts of their items, threshold, emit hits.
 struct SplitArgs {

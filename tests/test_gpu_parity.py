@@ -215,11 +215,11 @@ def test_empty_and_tiny_documents():
 
 
 def test_split_long_queries_small_batch():
-    # A batch of a few long queries: each query of more than 4080 windows runs as
-    # parts of 4080 terms whose partial counts are summed before the threshold.
-    # Edge cases: exactly 4080 and 4081 windows (one part / two parts), a
-    # periodic query whose distinct terms fill only the first part (the other
-    # parts count zero terms), K = 1 and K = 1000 permille.
+    # A batch of a few long queries: each query longer than the part size (256 to
+    # 4,080 terms, sized from the batch) runs as parts whose partial counts are
+    # summed before the threshold.  Edge cases: a periodic query whose distinct
+    # terms fill only its first part (the other parts count zero terms), windows
+    # with non-ACGT bytes, K = 1 and K = 1000 permille, 4,080 and 4,081 windows.
     lens = synth.lognormal_lengths(61, 400, 25000, 0.5, 5000, 200000)
     docs, off = synth.dna_docs(61, lens)
     qb, qo, src = synth.dna_queries(62, 20, docs, off, n_tp=14, median=12000, sigma=0.8, lo=4000, hi=60000,
@@ -229,6 +229,7 @@ def test_split_long_queries_small_batch():
     ql[0] = ql[0][:4080 + k - 1] if len(ql[0]) >= 4081 + k - 1 else ql[0]
     ql[1] = ql[1][:4081 + k - 1] if len(ql[1]) >= 4081 + k - 1 else ql[1]
     ql[2] = ql[2][:60] * 200
+    ql[4] = ql[4][:1000] + b"N" * 40 + ql[4][1000:]
     qo2 = np.zeros(21, np.uint64)
     qo2[1:] = np.cumsum([len(x) for x in ql])
     qb2 = np.frombuffer(b"".join(ql), np.uint8)
@@ -237,15 +238,20 @@ def test_split_long_queries_small_batch():
     ref = oracle_index(wl)
     dix = device_index(wl)
     assert_index_equal(dix, ref)
-    n_long = sum(1 for x in ql if len(x) - k + 1 > 4080)
-    assert n_long >= 10
-    for split, want in ((0, n_long), (2, n_long), (1, 0)):
+    windows = [max(0, len(x) - k + 1) for x in ql]
+    for split in (0, 2, 1):
         eng = cobs.Engine(dix, split=split)
         for flags in (cobs.COBS_BATCHED, cobs.COBS_GRAPH):
             got = eng.query_host(qb2, qo2, thr, flags)
-            assert eng.stats()["split_queries"] == want
+            st = eng.stats()
+            if split == 1:
+                assert st["split_queries"] == 0 and st["split_part"] == 0
+            else:
+                P = st["split_part"]
+                assert 256 <= P <= 4080 and P % 16 == 0
+                assert st["split_queries"] == sum(1 for w in windows if w > P) > 0
             assert_results_equal(got, ref, ql, thr)
-    for i in range(3, 20):
+    for i in range(5, 20):
         if src[i] >= 0 and thr[i] <= 700:
             assert src[i] in got[i][2].tolist()
 
