@@ -564,7 +564,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", default="cfg2")
-    ap.add_argument("--form", default="batched", choices=["batched", "graph"])
+    ap.add_argument("--form", default="graph", choices=["batched", "graph"],
+                    help="graph: the batched launch sequence captured once and replayed (default)")
     ap.add_argument("--slice-bytes", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--autotune", action="store_true")

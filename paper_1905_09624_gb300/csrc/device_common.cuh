@@ -57,51 +57,7 @@ __device__ __forceinline__ uint32_t barrett_mod(uint64_t x, uint64_t m, uint32_t
     return (uint32_t)(r >= w ? r - w : r);
 }
 
-// 2-bit code of a DNA byte: A=0 C=1 G=2 T=3, 4 = not a base.
-__device__ __forceinline__ uint32_t base2(uint8_t c) {
-    switch (c) {
-        case 'A': return 0u;
-        case 'C': return 1u;
-        case 'G': return 2u;
-        case 'T': return 3u;
-        default: return 4u;
-    }
-}
-
 __device__ __forceinline__ uint64_t kmer_mask(uint32_t k) { return k >= 32 ? ~0ULL : ((1ULL << (2 * k)) - 1ULL); }
-
-// Rolling window state for one thread walking positions left to right.
-// fwd: forward code of the last k bases (first base most significant);
-// rc: code of their reverse complement; run: consecutive valid bases seen.
-struct Roller {
-    uint64_t fwd, rc, bytes;
-    uint32_t run;
-};
-
-__device__ __forceinline__ void roll_init(Roller &r) { r.fwd = 0; r.rc = 0; r.bytes = 0; r.run = 0; }
-
-// Push byte c; returns true when the window of length k ending at c is a term,
-// and writes its code to *code.
-__device__ __forceinline__ bool roll_push(Roller &r, uint8_t c, uint32_t kind, uint32_t k, uint64_t mask,
-                                          uint64_t *code) {
-    if (kind == KIND_BYTES) {
-        // q bytes little-endian: the newest byte is the most significant of the window.
-        r.bytes = (r.bytes >> 8) | ((uint64_t)c << 56);
-        r.run = r.run < k ? r.run + 1 : k;
-        if (r.run < k) return false;
-        *code = k >= 8 ? r.bytes : (r.bytes >> (64 - 8 * k));
-        return true;
-    }
-    uint32_t b = base2(c);
-    if (b > 3u) { r.run = 0; return false; }
-    r.fwd = ((r.fwd << 2) | b) & mask;
-    // complement enters at the most significant end of the reverse complement
-    r.rc = (r.rc >> 2) | ((uint64_t)(3u - b) << (2 * (k - 1)));
-    r.run = r.run < k ? r.run + 1 : k;
-    if (r.run < k) return false;
-    *code = (kind == KIND_DNA_CANONICAL && r.rc < r.fwd) ? r.rc : r.fwd;
-    return true;
-}
 
 // ------------------------------------------------- packed base streams
 // A staged run of DNA bytes packed 16 bases per word: pk holds the 2-bit codes,

@@ -679,8 +679,7 @@ static void launch_L(const GatherArgs &a, uint32_t L, uint32_t grid, cudaStream_
 }
 
 uint32_t counter_levels_for(uint32_t max_terms) {
-    uint32_t bits = 0;
-    while (bits < 32 && (max_terms >> bits)) bits++;
+    const uint32_t bits = max_terms ? 32u - (uint32_t)__builtin_clz(max_terms) : 0u;  // bits of max_terms
     if (bits <= 8) return 8;
     if (bits <= 12) return 12;
     if (bits <= 16) return 16;

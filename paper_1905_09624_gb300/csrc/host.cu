@@ -967,7 +967,12 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
     eng->stat_tiles = 0;
     eng->stat_h2d_index_bytes = 0;
 
-    if (timed) CU(cudaEventRecord(eng->ev[0], s));
+    // timing events: inside a stream capture they must be external records to
+    // become event nodes of the graph
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(s, &cst));
+    const unsigned int tflag = cst == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (timed) CU(cudaEventRecordWithFlags(eng->ev[0], s, tflag));
     if (dix->streamed) CU(cudaEventRecord(eng->ev_fork, s));  // the copy stream joins here
     CU(cudaMemsetAsync(eng->qcount.p, 0, (uint8_t *)(ctr + n_ctr) - eng->qcount.as<uint8_t>(), s));
     CU(cudaMemcpyAsync(plan, eng->pin_plan.p, plan_bytes(bp), cudaMemcpyHostToDevice, s));
@@ -991,7 +996,7 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
 
     if (flags & COBS_PLAIN) {
         // One query per kernel sequence: terms, zero scores, gather, threshold.
-        if (timed) CU(cudaEventRecord(eng->ev[1], s));
+        if (timed) CU(cudaEventRecordWithFlags(eng->ev[1], s, tflag));
         for (uint64_t q = 0; q < n; q++) {
             ta.q0 = (uint32_t)q;
             launch_query_terms(ta, 1, s);
@@ -1028,7 +1033,7 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
             eng->stat_gather_launches += chunks ? 1 : 0;
         }
         CU(cudaGetLastError());
-        if (timed) CU(cudaEventRecord(eng->ev[2], s));
+        if (timed) CU(cudaEventRecordWithFlags(eng->ev[2], s, tflag));
     } else {
         ta.q0 = 0;
         if (!bp.long_q.empty()) {
@@ -1048,7 +1053,7 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
         launch_query_terms(ta, (uint32_t)n, s);
         eng->stat_launches += 1;
         CU(cudaGetLastError());
-        if (timed) CU(cudaEventRecord(eng->ev[1], s));
+        if (timed) CU(cudaEventRecordWithFlags(eng->ev[1], s, tflag));
         const uint32_t qpw = 32 / eng->lanes_per_query;
         const uint32_t grid = (uint32_t)eng->n_sm * eng->ctas_per_sm;
         // several counter classes: each on its own stream, forked after the terms
@@ -1153,7 +1158,7 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
             eng->stat_launches += 1;
         }
         CU(cudaGetLastError());
-        if (timed) CU(cudaEventRecord(eng->ev[2], s));
+        if (timed) CU(cudaEventRecordWithFlags(eng->ev[2], s, tflag));
     }
     HitsArgs ha{};
     ha.n_queries = (uint32_t)n;
@@ -1176,7 +1181,7 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
     launch_hits_finalize(ha, s);
     eng->stat_launches += 3;
     CU(cudaGetLastError());
-    if (timed) CU(cudaEventRecord(eng->ev[3], s));
+    if (timed) CU(cudaEventRecordWithFlags(eng->ev[3], s, tflag));
     CU(cudaMemcpyAsync(eng->pin_count.p, ctr, 8, cudaMemcpyDeviceToHost, s));
     return COBS_OK;
 }
@@ -1254,7 +1259,8 @@ cobs_status engine_query(cobs_engine *eng, const uint8_t *d_bytes, const uint64_
             }
             cudaGraph_t g = nullptr;
             CU(cudaStreamBeginCapture(eng->stream, cudaStreamCaptureModeThreadLocal));
-            cobs_status st = enqueue(eng, d_bytes, d_off, d_thr, COBS_BATCHED, false);
+            // the phase events become event-record nodes of the graph
+            cobs_status st = enqueue(eng, d_bytes, d_off, d_thr, COBS_BATCHED, true);
             cudaError_t ce = cudaStreamEndCapture(eng->stream, &g);
             if (st != COBS_OK) {
                 if (g) cudaGraphDestroy(g);
@@ -1272,9 +1278,7 @@ cobs_status engine_query(cobs_engine *eng, const uint8_t *d_bytes, const uint64_
             eng->graph_stats[1] = eng->stat_gather_launches;
             eng->graph_stats[2] = eng->stat_tiles;
         }
-        CU(cudaEventRecord(eng->ev[0], eng->stream));
         CU(cudaGraphLaunch(eng->gexec, eng->stream));
-        CU(cudaEventRecord(eng->ev[3], eng->stream));
         // kernels inside the graph
         eng->stat_launches = eng->graph_stats[0];
         eng->stat_gather_launches = eng->graph_stats[1];
@@ -1442,10 +1446,7 @@ extern "C" cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out
     TRY(engine_finish(eng));
     memset(out, 0, sizeof *out);
     float t = 0;
-    if (eng->last_flags & COBS_GRAPH) {
-        cudaEventElapsedTime(&t, eng->ev[0], eng->ev[3]);
-        out->ms_total = t;
-    } else if (eng->bp.n) {
+    if (eng->bp.n) {  // batched and graph forms: phase events; plain: ev[1] after the last terms launch
         cudaEventElapsedTime(&t, eng->ev[0], eng->ev[1]); out->ms_terms = t;
         cudaEventElapsedTime(&t, eng->ev[1], eng->ev[2]); out->ms_gather = t;
         cudaEventElapsedTime(&t, eng->ev[2], eng->ev[3]); out->ms_hits = t;
