@@ -498,8 +498,14 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_gather_pipe(GatherArgs a) {
 // The pipelined kernel for H = 2..4 hashes: a stage holds PH_G terms x H rows
 // per lane (row i of term j at position j * H + i); the consumer ANDs the H
 // rows of each term (Sec. 2.2) and feeds the PH_G indicator words to a
-// Harley-Seal tree of 8.  The ring lives in dynamic shared memory.
-constexpr int PH_G = 8, PH_D = 2, PH_WARPS = 2, PH_THREADS = PH_WARPS * 32;
+// Harley-Seal tree.  The ring lives in dynamic shared memory.  Stages of 4
+// terms keep the ring at 24 KB per CTA for h = 3 (8 CTAs/SM); stages of 8
+// (48 KB, 4 CTAs/SM) were 13 % slower on the text workload.
+#ifndef COBS_PH_G
+#define COBS_PH_G 4
+#endif
+constexpr int PH_G = COBS_PH_G, PH_D = 2, PH_WARPS = 2, PH_THREADS = PH_WARPS * 32;
+static_assert(PH_G == 4 || PH_G == 8, "stages of 4 or 8 terms");
 template <int H>
 constexpr size_t pipe_h_smem() { return (size_t)PH_WARPS * PH_D * PH_G * H * 32 * sizeof(uint4); }
 
@@ -513,6 +519,12 @@ __device__ __forceinline__ W4 and_rows(const uint4 *st, int j) {
         for (int w = 0; w < 4; w++) x.v[w] &= y.v[w];
     }
     return x;
+}
+template <int L, int H>
+__device__ __forceinline__ W4 hs4_and_stage(uint32_t (&lv)[4][L], const uint4 *st) {
+    const W4 tA = csa_lv<0>(lv, and_rows<H>(st, 0), and_rows<H>(st, 1));
+    const W4 tB = csa_lv<0>(lv, and_rows<H>(st, 2), and_rows<H>(st, 3));
+    return csa_lv<1>(lv, tA, tB);
 }
 template <int L, int H>
 __device__ __forceinline__ W4 hs8_and_stage(uint32_t (&lv)[4][L], const uint4 *st) {
@@ -615,7 +627,7 @@ __global__ void __launch_bounds__(PH_THREADS) k_gather_pipe_h(GatherArgs a) {
             load_idx_h<H>(ridx, gi, ng, ra, pol_idx);
         }
         uint32_t sc = 0;  // stage being consumed
-        CarryPairs<3, L> carry;
+        CarryPairs<PH_G == 8 ? 3 : 2, L> carry;
         for (uint32_t g = 0; g < ng; g++) {
             if (gi < ng) issue_stage_h<H>(ring + si * STAGE, colbase, rowbytes, ra, gi * PH_G, n, pol_row);
             cp_async_commit();
@@ -623,7 +635,8 @@ __global__ void __launch_bounds__(PH_THREADS) k_gather_pipe_h(GatherArgs a) {
             si = si + 1 == PH_D ? 0 : si + 1;
             load_idx_h<H>(ridx, gi, ng, ra, pol_idx);
             cp_async_wait<PH_D - 1>();
-            carry.add(lv, hs8_and_stage<L, H>(lv, ring + sc * STAGE));
+            if constexpr (PH_G == 8) carry.add(lv, hs8_and_stage<L, H>(lv, ring + sc * STAGE));
+            else carry.add(lv, hs4_and_stage<L, H>(lv, ring + sc * STAGE));
             sc = sc + 1 == PH_D ? 0 : sc + 1;
         }
         carry.flush(lv);
