@@ -115,3 +115,42 @@ def test_budget_admission_and_errors(served):
     assert cobs.lib().cobs_serve_poll(srv.h, 987654321, h) == cobs.COBS_ERR_NOT_FOUND
     stats = srv.stop()
     assert stats["rejected"] >= 1 and stats["completed"] == len(small)
+
+
+def test_wave_timeout_fails_its_tickets_and_the_server_recovers():
+    # A 1 ms wait limit that a wave cannot meet: one query of 2 M windows on an
+    # index of 313 blocks (its row pass alone takes far longer).  The ticket fails
+    # with COBS_ERR_TIMEOUT while the device work finishes on its own (the slot
+    # is reused only after that); later requests complete and match the batched
+    # form.
+    wl = small_compact(seed=83, n_docs=40000, median=500, sigma=0.3, lo=100, hi=2000, block_docs=128, n_q=8,
+                       q_len=300)
+    dix = device_index(wl)
+    assert len(dix.info()["blocks"]) == 313
+    rng = np.random.default_rng(5)
+    big = bytes(rng.choice(np.frombuffer(b"ACGT", np.uint8), 2_000_030))
+    srv = cobs.Server(dix, max_inflight_waves=2, wait_timeout_ms=1)
+    t = srv.submit(big, 900)
+    t0 = time.time()
+    with pytest.raises(cobs.CobsError) as e:
+        while srv.poll(t) is None:
+            assert time.time() - t0 < 60, "ticket did not resolve"
+            time.sleep(0.001)
+    assert e.value.status == cobs.COBS_ERR_TIMEOUT
+    # the server still answers: a short query completes (retried while the
+    # device finishes the timed-out work) with the batched form's result
+    ql = wl.query_list()
+    want = dix.query(wl.queries, wl.q_off, wl.thresholds, cobs.COBS_BATCHED)
+    for attempt in range(100):
+        try:
+            got = _wait(srv, [srv.submit(ql[0], int(wl.thresholds[0]))])[0]
+            break
+        except cobs.CobsError as e:
+            assert e.status == cobs.COBS_ERR_TIMEOUT
+            time.sleep(0.05)
+    else:
+        raise AssertionError("no request completed after the timeout")
+    assert (got[0], got[1]) == (want[0][0], want[0][1])
+    assert np.array_equal(got[2], want[0][2]) and np.array_equal(got[3], want[0][3])
+    stats = srv.stop()
+    assert stats["completed"] >= 1
