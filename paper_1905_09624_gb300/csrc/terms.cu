@@ -323,14 +323,96 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_terms_long_insert(TermsArgs a
                  a.tables + a.table_base[q], cap, a.codes + a.term_base[q], &a.ell[q], &a.long_flag[q], fr);
 }
 
-// Long queries, rows: one CTA per (long query, group of BP blocks).
+// Long queries, rows: one CTA per (long query, group of BP blocks).  With one
+// hash the scatter runs in chunks of LR_CHUNK terms: the chunk's rows of a block
+// are sorted by bucket in shared memory, and each bucket's run is written to its
+// place in one contiguous piece (the plain scatter writes one 4-byte row per
+// lane to 32 places).
+constexpr uint32_t LR_PER_THREAD = 4;
+constexpr uint32_t LR_CHUNK = TERMS_THREADS * LR_PER_THREAD;
 __global__ void __launch_bounds__(TERMS_THREADS) k_terms_long_rows(TermsArgs a) {
     __shared__ uint32_t s_hist[BP * TERMS_BUCKETS];
     __shared__ uint32_t s_shift[BP];
+    __shared__ uint32_t s_lh[TERMS_BUCKETS];   // chunk: bucket counts, then exclusive offsets
+    __shared__ uint32_t s_stage[LR_CHUNK];     // chunk rows in bucket order
     const uint32_t q = a.long_q[blockIdx.x];
     const uint32_t b0 = blockIdx.y * BP;
+    const uint32_t nbp = a.n_blocks - b0 < BP ? a.n_blocks - b0 : BP;
     const uint64_t base = a.term_base[q];
-    row_pass(a, a.codes + base, a.ell[q], base, b0, a.n_blocks - b0 < BP ? a.n_blocks - b0 : BP, s_hist, s_shift);
+    const unsigned long long *list = a.codes + base;
+    const uint32_t ell = a.ell[q];
+    if (a.h != 1) {
+        row_pass(a, list, ell, base, b0, nbp, s_hist, s_shift);
+        return;
+    }
+    // bucket counts of every block of the group, then global offsets
+    for (uint32_t i = threadIdx.x; i < nbp * TERMS_BUCKETS; i += blockDim.x) s_hist[i] = 0;
+    if (threadIdx.x < nbp) {
+        const uint32_t w = a.blocks[b0 + threadIdx.x].w;
+        const int lg = 32 - __clz(w > 1 ? w - 1 : 0);
+        s_shift[threadIdx.x] = lg > (int)TERMS_BUCKET_BITS ? (uint32_t)(lg - TERMS_BUCKET_BITS) : 0u;
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < ell; t += blockDim.x) {
+        const uint64_t h0 = list[t];
+#pragma unroll
+        for (uint32_t j = 0; j < BP; j++) {
+            if (j < nbp) {
+                const DevBlock blk = a.blocks[b0 + j];
+                atomicAdd(&s_hist[j * TERMS_BUCKETS + (barrett_mod(h0, blk.barrett_m, blk.w) >> s_shift[j])], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    const uint32_t warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    for (uint32_t j = warp; j < nbp; j += n_warps) scan_hist(s_hist + j * TERMS_BUCKETS);
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < ell; c0 += LR_CHUNK) {
+        const uint32_t cn = ell - c0 < LR_CHUNK ? ell - c0 : LR_CHUNK;
+        uint64_t h0[LR_PER_THREAD];
+#pragma unroll
+        for (uint32_t i = 0; i < LR_PER_THREAD; i++) {
+            const uint32_t t = c0 + i * blockDim.x + threadIdx.x;
+            h0[i] = t < ell ? list[t] : 0ULL;
+        }
+        for (uint32_t j = 0; j < nbp; j++) {
+            const DevBlock blk = a.blocks[b0 + j];
+            const uint32_t sh = s_shift[j];
+            uint32_t *gh = s_hist + j * TERMS_BUCKETS;  // next free position of each bucket
+            if (threadIdx.x < TERMS_BUCKETS) s_lh[threadIdx.x] = 0;
+            __syncthreads();
+            uint32_t r[LR_PER_THREAD], rank[LR_PER_THREAD];
+#pragma unroll
+            for (uint32_t i = 0; i < LR_PER_THREAD; i++) {
+                const uint32_t t = c0 + i * blockDim.x + threadIdx.x;
+                r[i] = barrett_mod(h0[i], blk.barrett_m, blk.w);
+                rank[i] = t < ell ? atomicAdd(&s_lh[r[i] >> sh], 1u) : 0u;
+            }
+            __syncthreads();
+            if (warp == 0) scan_hist(s_lh);  // counts -> exclusive offsets
+            __syncthreads();
+#pragma unroll
+            for (uint32_t i = 0; i < LR_PER_THREAD; i++) {
+                const uint32_t t = c0 + i * blockDim.x + threadIdx.x;
+                if (t < ell) s_stage[s_lh[r[i] >> sh] + rank[i]] = r[i];
+            }
+            __syncthreads();
+            // staged position x of bucket b goes to gh[b] + (x - s_lh[b])
+            uint32_t *dst = a.rows_idx + (uint64_t)(b0 + j) * a.tcap + base;
+            for (uint32_t x = threadIdx.x; x < cn; x += blockDim.x) {
+                const uint32_t rv = s_stage[x];
+                const uint32_t b = rv >> sh;
+                dst[gh[b] + (x - s_lh[b])] = rv;
+            }
+            __syncthreads();
+            if (threadIdx.x < TERMS_BUCKETS) {  // advance each bucket by the chunk's count
+                const uint32_t b = threadIdx.x;
+                const uint32_t next = b + 1 < TERMS_BUCKETS ? s_lh[b + 1] : cn;
+                gh[b] += next - s_lh[b];
+            }
+            __syncthreads();
+        }
+    }
 }
 
 void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s) {
