@@ -247,6 +247,17 @@ cobs_status cobs_engine_query_device(cobs_engine *eng, const uint8_t *queries_de
 cobs_status cobs_engine_query_host(cobs_engine *eng, const uint8_t *queries, const uint64_t *offsets,
                                    const uint16_t *thr, uint64_t n, uint32_t flags, cobs_result **out);
 
+/* The same without waiting: queues the copies of the host inputs and the query
+ * on the engine stream and returns; cobs_engine_download (or _results_device,
+ * _stats) waits and collects.  Offsets and thresholds are copied before the
+ * call returns; query bytes in page-locked memory are read by DMA from the
+ * caller's buffer, which must stay unchanged until the results are collected
+ * (pageable bytes are staged before the call returns).  Engines on different
+ * streams pipeline batches: one engine's copies and host planning overlap
+ * another's kernels. */
+cobs_status cobs_engine_submit_host(cobs_engine *eng, const uint8_t *queries, const uint64_t *offsets,
+                                    const uint16_t *thr, uint64_t n, uint32_t flags);
+
 /* Device pointers to the last query's results (valid until the next query):
  * n_terms[n], min_score[n], hit_offsets[n+1] (u64), hit_ids[total], hit_scores[total]. */
 cobs_status cobs_engine_results_device(cobs_engine *eng, const uint32_t **n_terms, const uint32_t **min_score,

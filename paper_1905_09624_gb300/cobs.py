@@ -112,6 +112,7 @@ _PROTOS = {
     "cobs_engine_query_device": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.c_uint64, ctypes.c_uint32]),
     "cobs_engine_query_host": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_uint64, ctypes.c_uint32,
                                               ctypes.POINTER(ctypes.POINTER(cobs_result))]),
+    "cobs_engine_submit_host": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_uint64, ctypes.c_uint32]),
     "cobs_engine_results_device": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                                   ctypes.POINTER(vp), ctypes.POINTER(vp)]),
     "cobs_engine_download": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.POINTER(cobs_result))]),
@@ -371,6 +372,16 @@ class Engine:
         check(lib().cobs_engine_query_host(self.h, _ptr(queries), _ptr(q_off), _ptr(thr), len(q_off) - 1, flags,
                                            ctypes.byref(res)), "cobs_engine_query_host")
         return result_to_python(res)
+
+    def submit_host(self, queries, q_off, thr, flags=COBS_BATCHED):
+        """cobs_engine_submit_host: queue copies and query, return at once; collect
+        with download / download_arrays.  Pinned query bytes must stay unchanged
+        until then."""
+        self._inputs = (np.ascontiguousarray(queries, dtype=np.uint8), np.ascontiguousarray(q_off, dtype=np.uint64),
+                        np.ascontiguousarray(thr, dtype=np.uint16))  # kept alive until the next submit
+        qb, qo, th = self._inputs
+        check(lib().cobs_engine_submit_host(self.h, _ptr(qb), _ptr(qo), _ptr(th), len(qo) - 1, flags),
+              "cobs_engine_submit_host")
 
     def query_host_arrays(self, queries, q_off, thr, flags=COBS_BATCHED):
         """cobs_engine_query_host, results as flat arrays (see result_to_arrays)."""

@@ -1399,7 +1399,15 @@ static cobs_status check_thresholds(const uint16_t *thr, uint64_t n) {
 
 extern "C" cobs_status cobs_engine_query_host(cobs_engine *eng, const uint8_t *queries, const uint64_t *offsets,
                                               const uint16_t *thr, uint64_t n, uint32_t flags, cobs_result **out) {
-    if (!eng || !offsets || !out || (n && (!thr || !queries))) return set_error(COBS_ERR_ARG, "NULL argument");
+    if (!out) return set_error(COBS_ERR_ARG, "NULL argument");
+    TRY(cobs_engine_submit_host(eng, queries, offsets, thr, n, flags));
+    return cobs_engine_download(eng, out);
+}
+
+extern "C" cobs_status cobs_engine_submit_host(cobs_engine *eng, const uint8_t *queries, const uint64_t *offsets,
+                                               const uint16_t *thr, uint64_t n, uint32_t flags) {
+    if (!eng || !offsets || (n && (!thr || !queries))) return set_error(COBS_ERR_ARG, "NULL argument");
+    TRY(engine_finish(eng));  // the staging buffers of a previous batch are free again
     TRY(check_thresholds(thr, n));
     CU(cudaSetDevice(eng->dix->device));
     const uint64_t total = offsets[n];
@@ -1422,9 +1430,8 @@ extern "C" cobs_status cobs_engine_query_host(cobs_engine *eng, const uint8_t *q
     if (total) CU(cudaMemcpyAsync(eng->qbytes.p, pinned ? queries : pin, total, cudaMemcpyHostToDevice, s));
     CU(cudaMemcpyAsync(eng->qoff.p, pin + o1, (n + 1) * 8, cudaMemcpyHostToDevice, s));
     if (n) CU(cudaMemcpyAsync(eng->thr.p, pin + o2, n * 2, cudaMemcpyHostToDevice, s));
-    TRY(engine_query(eng, eng->qbytes.as<uint8_t>(), eng->qoff.as<uint64_t>(), offsets, eng->thr.as<uint16_t>(), n,
-                     flags));
-    return cobs_engine_download(eng, out);
+    return engine_query(eng, eng->qbytes.as<uint8_t>(), eng->qoff.as<uint64_t>(), offsets, eng->thr.as<uint16_t>(), n,
+                        flags);
 }
 
 extern "C" cobs_status cobs_query_batch(cobs_device_index *dix, const uint8_t *queries, const uint64_t *query_offsets,

@@ -285,3 +285,34 @@ def test_all_ones_qgram_short_and_long_queries():
             got = dix.query(qb, qo, thr, flags)
             assert_results_equal(got, ref, qs, thr)
             assert got[2][0] == 1 and got[3][0] == 1  # one distinct term each
+
+
+def test_submit_host_pipelined_on_two_engines(compact):
+    # Two engines on two streams alternate cobs_engine_submit_host and
+    # cobs_engine_download over four sub-batches (one of them from page-locked
+    # memory): each batch's results equal the oracle's.
+    import torch
+    wl, ref, dix = compact
+    ql = wl.query_list()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    engs = [cobs.Engine(dix, stream=s1.cuda_stream), cobs.Engine(dix, stream=s2.cuda_stream)]
+    cuts = [0, 40, 41, 100, len(ql)]
+    batches = []
+    for lo, hi in zip(cuts, cuts[1:]):
+        qs = ql[lo:hi]
+        off = np.zeros(len(qs) + 1, np.uint64)
+        off[1:] = np.cumsum([len(x) for x in qs])
+        qb = np.frombuffer(b"".join(qs), np.uint8)
+        if lo == 41:  # page-locked query bytes: copied by DMA from this buffer
+            pin = torch.empty(len(qb), dtype=torch.uint8, pin_memory=True).numpy()
+            pin[:] = qb
+            qb = pin
+        batches.append((qs, qb, off, wl.thresholds[lo:hi]))
+    for flags in (cobs.COBS_BATCHED, cobs.COBS_GRAPH):
+        engs[0].submit_host(batches[0][1], batches[0][2], batches[0][3], flags)
+        for i in range(1, len(batches) + 1):
+            if i < len(batches):
+                qs, qb, off, thr = batches[i]
+                engs[i % 2].submit_host(qb, off, thr, flags)
+            qs, qb, off, thr = batches[i - 1]
+            assert_results_equal(engs[(i - 1) % 2].download(), ref, qs, thr)
