@@ -523,6 +523,29 @@ def run_gpu(args):
                  "steps": args.streamed_steps, "parts": 2, "blocks": len(view.info()["blocks"]),
                  "row_gbs_logical": m_rows / args.streamed_steps / (mm / 1e3) / 1e9}
         del meng, view, parts
+    # ---- incremental insertion: 5 % more documents of the same length law
+    insert = None
+    if not args.skip_insert and wl.n_docs >= 20:
+        n_new = max(1, wl.n_docs // 20)
+        lens = (wl.doc_off[1:] - wl.doc_off[:-1]).astype(np.int64)
+        rng = np.random.default_rng(4242)
+        new_lens = rng.choice(lens, n_new)
+        if wl.term_kind == 2:
+            words, word_off = synth.vocab(4244, 2000)
+            new_docs, new_off = synth.text_docs(4243, new_lens.astype(np.uint64), words, word_off)
+        else:
+            new_docs, new_off = synth.dna_docs(4243, new_lens.astype(np.uint64))
+        host_ix = dix.download()
+        t0 = time.perf_counter()
+        ins = host_ix.insert(new_docs, new_off, device=local)
+        t_ins = time.perf_counter() - t0
+        ii = ins.info()
+        insert = {"new_docs": int(n_new), "new_bytes": int(new_off[-1]), "seconds": t_ins,
+                  "blocks_before": len(info["blocks"]), "blocks_after": len(ii["blocks"]),
+                  "into_free_columns": int(sum(b["n_docs"] for b in ii["blocks"][:len(info["blocks"])]) - wl.n_docs),
+                  "note": "cobs_index_insert on the host index: the time includes copying the index to the "
+                          "device and back"}
+        del ins, host_ix
     sampler.stop()
     clocks = sampler.summary(t_wall0, t_wall1)
 
@@ -568,7 +591,7 @@ def run_gpu(args):
                      "gbs_with_h2d": int(wl.doc_off[-1]) / build_h2d_s / 1e9,
                      "index_bytes": info["rows_bytes"], "blocks": len(info["blocks"])},
            "speedup_batched_over_plain": (value / plain["value"]) if plain else None,
-           "streamed": streamed, "multi_index": multi}
+           "streamed": streamed, "multi_index": multi, "insert": insert}
     if plain:
         out["plain"]["frac_of_hbm_peak"] = plain["row_gbs_logical"] / peak
 
@@ -607,6 +630,7 @@ def main():
     ap.add_argument("--skip-streamed", action="store_true", help="skip the streamed-index measurement")
     ap.add_argument("--streamed-steps", type=int, default=10, help="timed steps of the streamed and multi-index runs")
     ap.add_argument("--skip-multi", action="store_true", help="skip the multi-index measurement")
+    ap.add_argument("--skip-insert", action="store_true", help="skip the incremental-insertion measurement")
     ap.add_argument("--stage-bytes", type=int, default=0, help="streamed index: device staging bytes (0 = 2 slots)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-queries", type=int, default=400)

@@ -175,6 +175,20 @@ cobs_status cobs_index_load(const char *path, cobs_index **out);
  * two.  Host memory only; a and b are unchanged. */
 cobs_status cobs_index_merge(const cobs_index *a, const cobs_index *b, cobs_index **out);
 
+/* Incremental insertion (Sec. 2.3: new documents packed into the best block
+ * with free room): a new host index holding ix's documents and n_docs more
+ * (document j of the new list gets id n_docs(ix) + j).  The distinct-term count
+ * v of every new document is computed on `device`; in input order each goes to
+ * a free column of the block whose largest count is the smallest one still at
+ * least v (the block's Bloom size then keeps the false-positive rate; free
+ * columns are the row padding up to a multiple of 128 documents), ties to the
+ * lower block, appended after the block's documents.  The documents no block
+ * takes form new blocks after the old ones, planned as a build over them alone
+ * (the block size, p and width of ix's parameters).  Bits are set on the device
+ * by the build kernels; ix is unchanged.  Errors: ARG, OOM, CUDA. */
+cobs_status cobs_index_insert(const cobs_index *ix, const uint8_t *docs, const uint64_t *doc_offsets,
+                              uint64_t n_docs, int device, cobs_index **out);
+
 /* Inspect a host index.  Pointers stay valid until cobs_index_free.
  * perm[i] = original id of the document at sorted position i;
  * nterms[d] = distinct terms of original document d. */

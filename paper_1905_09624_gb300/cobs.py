@@ -94,6 +94,7 @@ _PROTOS = {
     "cobs_load_device_streamed": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.POINTER(vp)]),
     "cobs_multi_index_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_uint64, ctypes.POINTER(vp)]),
     "cobs_index_merge": (ctypes.c_int, [vp, vp, ctypes.POINTER(vp)]),
+    "cobs_index_insert": (ctypes.c_int, [vp, vp, vp, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(vp)]),
     "cobs_index_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
     "cobs_index_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(vp)]),
     "cobs_index_info": (ctypes.c_int, [vp, ctypes.POINTER(cobs_params), u64p, u64p,
@@ -253,6 +254,15 @@ class HostIndex:
     def load(path):
         h = vp()
         check(lib().cobs_index_load(path.encode(), ctypes.byref(h)), "cobs_index_load")
+        return HostIndex(h.value)
+
+    def insert(self, docs, doc_off, device=0):
+        """cobs_index_insert: a new index with documents added (ids after self's)."""
+        docs = np.ascontiguousarray(docs, dtype=np.uint8)
+        doc_off = np.ascontiguousarray(doc_off, dtype=np.uint64)
+        h = vp()
+        check(lib().cobs_index_insert(self.h, _ptr(docs) if len(docs) else None, _ptr(doc_off), len(doc_off) - 1,
+                                      device, ctypes.byref(h)), "cobs_index_insert")
         return HostIndex(h.value)
 
     def merge(self, other):

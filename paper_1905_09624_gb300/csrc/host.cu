@@ -142,13 +142,14 @@ static cobs_status upload_tables(cobs_device_index *dix, cudaStream_t s) {
 
 // ------------------------------------------------------------ device build
 
-static cobs_status build_impl(const cobs_params *P, const uint8_t *d_docs, const uint64_t *d_off,
-                              const uint64_t *h_off, uint64_t n_docs, int device, cudaStream_t s,
-                              cobs_device_index **out) {
-    TRY(check_params(P));
+// Distinct-term counts v[d] of documents on the device (the sizes of Sec. 2.3,
+// determined before the blocks are planned), and their window counts npos[d].
+static cobs_status count_terms(const cobs_params *P, const uint8_t *d_docs, const uint64_t *d_off,
+                               const uint64_t *h_off, uint64_t n_docs, cudaStream_t s, std::vector<uint64_t> &npos,
+                               std::vector<uint64_t> &v) {
     if (n_docs >= 0xFFFFFFFFULL) return set_error(COBS_ERR_ARG, "n_docs must be < 2^32");
     const uint32_t k = P->q;
-    std::vector<uint64_t> npos(n_docs);
+    npos.assign(n_docs, 0);
     std::vector<uint32_t> chunk_doc;
     std::vector<uint64_t> chunk_p0;
     for (uint64_t d = 0; d < n_docs; d++) {
@@ -164,7 +165,7 @@ static cobs_status build_impl(const cobs_params *P, const uint8_t *d_docs, const
     const uint64_t n_chunks = chunk_doc.size();
     if (n_chunks > 0x7FFFFFFFULL) return set_error(COBS_ERR_ARG, "documents too large for one build");
 
-    DevBuf dchunk_doc, dchunk_p0, dv, dempty, dtbase, dtcap, dtables, ddocblk, ddoccol;
+    DevBuf dchunk_doc, dchunk_p0, dv, dempty, dtbase, dtcap, dtables;
     CU(dchunk_doc.ensure(n_chunks * 4));
     CU(dchunk_p0.ensure(n_chunks * 8));
     CU(dv.ensure(n_docs * 8));
@@ -232,10 +233,68 @@ static cobs_status build_impl(const cobs_params *P, const uint8_t *d_docs, const
         launch_doc_count(ca, (uint32_t)(wv.c1 - wv.c0), s);
         CU(cudaGetLastError());
     }
-    std::vector<uint64_t> v(n_docs);
+    v.assign(n_docs, 0);
     if (n_docs) CU(cudaMemcpyAsync(v.data(), dv.p, n_docs * 8, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    dtables.release();
+    return COBS_OK;
+}
+
+// Bloom bits of documents: document d goes to column doc_col[d] of block
+// doc_block[d] of the rows at rows32 (block table at dblocks).  Work in the
+// order `order` (documents by column: CTAs that run together set bits of
+// neighbouring columns, i.e. of the same 32-bit words of every row, so the words
+// being updated stay in L2).
+static cobs_status set_doc_bits(const cobs_params *P, const uint8_t *d_docs, const uint64_t *d_off,
+                                const std::vector<uint64_t> &npos, const std::vector<uint64_t> &order,
+                                const std::vector<uint32_t> &doc_block, const std::vector<uint32_t> &doc_col,
+                                const DevBlock *dblocks, uint32_t *rows32, cudaStream_t s) {
+    const uint64_t n_docs = npos.size();
+    DevBuf ddocblk, ddoccol, dchunk_doc, dchunk_p0;
+    CU(ddocblk.ensure(n_docs * 4));
+    CU(ddoccol.ensure(n_docs * 4));
+    if (n_docs) {
+        CU(cudaMemcpyAsync(ddocblk.p, doc_block.data(), n_docs * 4, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(ddoccol.p, doc_col.data(), n_docs * 4, cudaMemcpyHostToDevice, s));
+    }
+    std::vector<uint32_t> sb_doc;
+    std::vector<uint64_t> sb_p0;
+    for (uint64_t d : order)
+        for (uint64_t p = 0; p < npos[d]; p += SETBITS_CHUNK) {
+            sb_doc.push_back((uint32_t)d);
+            sb_p0.push_back(p);
+        }
+    const uint64_t n_sb = sb_doc.size();
+    if (n_sb > 0x7FFFFFFFULL) return set_error(COBS_ERR_ARG, "documents too large for one build");
+    CU(dchunk_doc.ensure(n_sb * 4));
+    CU(dchunk_p0.ensure(n_sb * 8));
+    if (n_sb) {
+        CU(cudaMemcpyAsync(dchunk_doc.p, sb_doc.data(), n_sb * 4, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(dchunk_p0.p, sb_p0.data(), n_sb * 8, cudaMemcpyHostToDevice, s));
+    }
+    SetBitsArgs sa{};
+    sa.docs = d_docs;
+    sa.doc_off = d_off;
+    sa.chunk_doc = dchunk_doc.as<uint32_t>();
+    sa.chunk_p0 = dchunk_p0.as<uint64_t>();
+    sa.doc_block = ddocblk.as<uint32_t>();
+    sa.doc_col = ddoccol.as<uint32_t>();
+    sa.blocks = dblocks;
+    sa.rows32 = rows32;
+    sa.kind = P->term_kind;
+    sa.k = P->q;
+    sa.h = P->num_hashes;
+    launch_doc_setbits(sa, (uint32_t)n_sb, s);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(s));  // the staging buffers above are freed on return
+    return COBS_OK;
+}
+
+static cobs_status build_impl(const cobs_params *P, const uint8_t *d_docs, const uint64_t *d_off,
+                              const uint64_t *h_off, uint64_t n_docs, int device, cudaStream_t s,
+                              cobs_device_index **out) {
+    TRY(check_params(P));
+    std::vector<uint64_t> npos, v;
+    TRY(count_terms(P, d_docs, d_off, h_off, n_docs, s, npos, v));
 
     // Plan on the host, then set the Bloom bits on the device.
     cobs_device_index *dix = new cobs_device_index();
@@ -261,47 +320,9 @@ static cobs_status build_impl(const cobs_params *P, const uint8_t *d_docs, const
             doc_block[d] = (uint32_t)b;
             doc_col[d] = (uint32_t)j;
         }
-    if ((ce = ddocblk.ensure(n_docs * 4)) != cudaSuccess || (ce = ddoccol.ensure(n_docs * 4)) != cudaSuccess)
-        return fail(set_error(COBS_ERR_OOM, "build tables: %s", cudaGetErrorString(ce)));
-    if (n_docs) {
-        cudaMemcpyAsync(ddocblk.p, doc_block.data(), n_docs * 4, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(ddoccol.p, doc_col.data(), n_docs * 4, cudaMemcpyHostToDevice, s);
-    }
-    // Bit-setting work in column order (block, sorted position): CTAs that run
-    // together set bits of neighbouring columns, i.e. of the same 32-bit words of
-    // every row, so the words being updated stay in L2.
-    std::vector<uint32_t> sb_doc;
-    std::vector<uint64_t> sb_p0;
-    for (uint64_t pos = 0; pos < n_docs; pos++) {
-        const uint64_t d = dix->perm[pos];
-        for (uint64_t p = 0; p < npos[d]; p += SETBITS_CHUNK) {
-            sb_doc.push_back((uint32_t)d);
-            sb_p0.push_back(p);
-        }
-    }
-    const uint64_t n_sb = sb_doc.size();
-    if (n_sb > 0x7FFFFFFFULL) return fail(set_error(COBS_ERR_ARG, "documents too large for one build"));
-    if ((ce = dchunk_doc.ensure(n_sb * 4)) != cudaSuccess || (ce = dchunk_p0.ensure(n_sb * 8)) != cudaSuccess)
-        return fail(set_error(COBS_ERR_OOM, "build chunk lists: %s", cudaGetErrorString(ce)));
-    if (n_sb) {
-        cudaMemcpyAsync(dchunk_doc.p, sb_doc.data(), n_sb * 4, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(dchunk_p0.p, sb_p0.data(), n_sb * 8, cudaMemcpyHostToDevice, s);
-    }
-    SetBitsArgs sa{};
-    sa.docs = d_docs;
-    sa.doc_off = d_off;
-    sa.chunk_doc = dchunk_doc.as<uint32_t>();
-    sa.chunk_p0 = dchunk_p0.as<uint64_t>();
-    sa.doc_block = ddocblk.as<uint32_t>();
-    sa.doc_col = ddoccol.as<uint32_t>();
-    sa.blocks = dix->dblocks.as<DevBlock>();
-    sa.rows32 = dix->rows.as<uint32_t>();
-    sa.kind = P->term_kind;
-    sa.k = k;
-    sa.h = P->num_hashes;
-    launch_doc_setbits(sa, (uint32_t)n_sb, s);
-    if ((ce = cudaGetLastError()) != cudaSuccess || (ce = cudaStreamSynchronize(s)) != cudaSuccess)
-        return fail(set_error(COBS_ERR_CUDA, "build kernels: %s", cudaGetErrorString(ce)));
+    st = set_doc_bits(P, d_docs, d_off, npos, dix->perm, doc_block, doc_col, dix->dblocks.as<DevBlock>(),
+                      dix->rows.as<uint32_t>(), s);
+    if (st != COBS_OK) return fail(st);
     *out = dix;
     return COBS_OK;
 }
@@ -511,6 +532,121 @@ extern "C" cobs_status cobs_device_index_info(const cobs_device_index *dix, cobs
     if (blocks) *blocks = dix->blocks.data();
     if (rows_dev) *rows_dev = (dix->streamed || dix->rows_view) ? nullptr : dix->rows.p;
     if (rows_bytes) *rows_bytes = dix->rows_bytes;
+    return COBS_OK;
+}
+
+// ------------------------------------------------------------------ insert
+extern "C" cobs_status cobs_index_insert(const cobs_index *ix, const uint8_t *docs, const uint64_t *doc_offsets,
+                                         uint64_t n_new, int device, cobs_index **out) {
+    if (!ix || !out || !doc_offsets || (n_new && !docs)) return set_error(COBS_ERR_ARG, "NULL argument");
+    TRY(check_params(&ix->params));
+    if (ix->n_docs + n_new >= 0xFFFFFFFFULL) return set_error(COBS_ERR_ARG, "n_docs must be < 2^32");
+    const cobs_params &P = ix->params;
+    CU(cudaSetDevice(device));
+    cudaStream_t s = nullptr;
+    const uint64_t total = doc_offsets[n_new];
+    DevBuf dd, doff;
+    CU(dd.ensure(total));
+    CU(doff.ensure((n_new + 1) * 8));
+    if (total) CU(cudaMemcpyAsync(dd.p, docs, total, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(doff.p, doc_offsets, (n_new + 1) * 8, cudaMemcpyHostToDevice, s));
+    std::vector<uint64_t> npos, v;
+    TRY(count_terms(&P, dd.as<uint8_t>(), doff.as<uint64_t>(), doc_offsets, n_new, s, npos, v));
+
+    // Best free block: the one with the smallest largest-document count that is
+    // still at least the new document's (its Bloom size keeps the rate) and has
+    // a free column; ties to the lower block.  New documents in input order.
+    const uint64_t n_old = ix->n_docs, nb_old = ix->blocks.size();
+    std::vector<uint64_t> free_cols(nb_old);
+    for (uint64_t b = 0; b < nb_old; b++) free_cols[b] = ix->blocks[b].rowbytes * 8 - ix->blocks[b].n_docs;
+    std::vector<std::vector<uint64_t>> added(nb_old);
+    std::vector<uint64_t> left;  // new documents no block takes
+    std::vector<uint32_t> doc_block(n_new), doc_col(n_new);
+    for (uint64_t j = 0; j < n_new; j++) {
+        int64_t best = -1;
+        for (uint64_t b = 0; b < nb_old; b++)
+            if (free_cols[b] && ix->blocks[b].max_terms >= v[j] &&
+                (best < 0 || ix->blocks[b].max_terms < ix->blocks[best].max_terms))
+                best = (int64_t)b;
+        if (best < 0) {
+            left.push_back(j);
+            continue;
+        }
+        doc_block[j] = (uint32_t)best;
+        doc_col[j] = (uint32_t)(ix->blocks[best].n_docs + added[best].size());
+        added[best].push_back(j);
+        free_cols[best]--;
+    }
+    // the rest form blocks of their own, planned like a build over them alone
+    std::vector<uint64_t> vl(left.size());
+    for (size_t i = 0; i < left.size(); i++) vl[i] = v[left[i]];
+    std::vector<cobs_block_info> nblocks;
+    std::vector<uint64_t> nperm;
+    TRY(plan_index(P, vl, nblocks, nperm));
+
+    cobs_index *res = new cobs_index();
+    res->params = P;
+    res->n_docs = n_old + n_new;
+    res->nterms = ix->nterms;
+    res->nterms.insert(res->nterms.end(), v.begin(), v.end());
+    uint64_t pos = 0;
+    for (uint64_t b = 0; b < nb_old; b++) {
+        cobs_block_info B = ix->blocks[b];
+        for (uint64_t i = 0; i < B.n_docs; i++) res->perm.push_back(ix->perm[B.doc_begin + i]);
+        for (uint64_t j : added[b]) res->perm.push_back(n_old + j);
+        B.doc_begin = pos;
+        B.n_docs += added[b].size();
+        pos += B.n_docs;
+        res->blocks.push_back(B);
+    }
+    const uint64_t old_bytes = ix->rows.size();
+    for (size_t nbi = 0; nbi < nblocks.size(); nbi++) {
+        cobs_block_info B = nblocks[nbi];
+        for (uint64_t i = 0; i < B.n_docs; i++) {
+            const uint64_t j = left[nperm[B.doc_begin + i]];
+            res->perm.push_back(n_old + j);
+            doc_block[j] = (uint32_t)(nb_old + nbi);
+            doc_col[j] = (uint32_t)i;
+        }
+        B.doc_begin = pos;
+        B.row_offset += old_bytes;
+        pos += B.n_docs;
+        res->blocks.push_back(B);
+    }
+    if (res->blocks.size() > 1 && res->params.block_docs == 0) {
+        uint64_t bmax = 0;
+        for (const auto &b : res->blocks) bmax = std::max(bmax, b.n_docs);
+        res->params.block_docs = bmax;  // several blocks: no longer one classic block
+    }
+    const uint64_t new_bytes = nblocks.empty() ? 0 : nblocks.back().row_offset + nblocks.back().w * nblocks.back().rowbytes;
+
+    // rows on the device: the old ones, the new blocks cleared, then the new bits
+    cobs_device_index tmp;
+    tmp.params = res->params;
+    tmp.device = device;
+    tmp.n_docs = res->n_docs;
+    tmp.blocks = res->blocks;
+    tmp.perm = res->perm;
+    tmp.rows_bytes = old_bytes + new_bytes;
+    auto fail = [&](cobs_status e) { delete res; return e; };
+    cudaError_t ce = tmp.rows.ensure(tmp.rows_bytes);
+    if (ce == cudaSuccess && old_bytes) ce = cudaMemcpyAsync(tmp.rows.p, ix->rows.data(), old_bytes, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess && new_bytes) ce = cudaMemsetAsync(tmp.rows.as<uint8_t>() + old_bytes, 0, new_bytes, s);
+    if (ce != cudaSuccess) return fail(set_error(COBS_ERR_OOM, "insert rows: %s", cudaGetErrorString(ce)));
+    cobs_status st = upload_tables(&tmp, s);
+    if (st != COBS_OK) return fail(st);
+    std::vector<uint64_t> order;  // by column: old blocks' new documents, then the new blocks
+    for (uint64_t b = 0; b < nb_old; b++) order.insert(order.end(), added[b].begin(), added[b].end());
+    for (size_t nbi = 0; nbi < nblocks.size(); nbi++)
+        for (uint64_t i = 0; i < nblocks[nbi].n_docs; i++) order.push_back(left[nperm[nblocks[nbi].doc_begin + i]]);
+    st = set_doc_bits(&P, dd.as<uint8_t>(), doff.as<uint64_t>(), npos, order, doc_block, doc_col,
+                      tmp.dblocks.as<DevBlock>(), tmp.rows.as<uint32_t>(), s);
+    if (st != COBS_OK) return fail(st);
+    res->rows.resize(tmp.rows_bytes);
+    if (tmp.rows_bytes &&
+        (ce = cudaMemcpy(res->rows.data(), tmp.rows.p, tmp.rows_bytes, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return fail(set_error(COBS_ERR_CUDA, "insert download: %s", cudaGetErrorString(ce)));
+    *out = res;
     return COBS_OK;
 }
 
