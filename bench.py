@@ -526,6 +526,7 @@ def run_gpu(args):
     # ---- incremental insertion: 5 % more documents of the same length law
     insert = None
     if not args.skip_insert and wl.n_docs >= 20:
+        import synth
         n_new = max(1, wl.n_docs // 20)
         lens = (wl.doc_off[1:] - wl.doc_off[:-1]).astype(np.int64)
         rng = np.random.default_rng(4242)
