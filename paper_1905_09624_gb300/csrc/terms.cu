@@ -155,12 +155,13 @@ __device__ __forceinline__ void scan_hist(uint32_t *hj) {
     }
 }
 
-// Row pass for blocks [b0, b0 + nbp), nbp <= BP: the distinct terms' rows in
+// Row pass for blocks [b0, b0 + nbp), nbp <= NB: the distinct terms' rows in
 // row-bucket order (a counting sort by the top bits of the hash-0 row).  Scores
 // do not depend on the order of the terms; bucketed order makes all warps of
 // the gather sweep the rows of a slice together, so the rows in use at any
 // moment form a narrow band.  list[t] is hash 0 (h == 1) or the code.  Every
 // thread of the CTA calls it.
+template <uint32_t NB>
 __device__ __forceinline__ void row_pass(const TermsArgs &a, const unsigned long long *list, uint32_t ell,
                                          uint64_t base, uint32_t b0, uint32_t nbp, uint32_t *s_hist,
                                          uint32_t *s_shift) {
@@ -182,7 +183,7 @@ __device__ __forceinline__ void row_pass(const TermsArgs &a, const unsigned long
     __syncthreads();
     each_distinct([&](uint64_t, uint64_t h0) {
 #pragma unroll
-        for (uint32_t j = 0; j < BP; j++) {
+        for (uint32_t j = 0; j < NB; j++) {
             if (j < nbp) {
                 const DevBlock blk = a.blocks[b0 + j];
                 const uint32_t r0 = barrett_mod(h0, blk.barrett_m, blk.w);
@@ -194,9 +195,9 @@ __device__ __forceinline__ void row_pass(const TermsArgs &a, const unsigned long
     for (uint32_t j = warp; j < nbp; j += n_warps) scan_hist(s_hist + j * TERMS_BUCKETS);
     __syncthreads();
     each_distinct([&](uint64_t code, uint64_t h0) {
-        uint32_t pos[BP];
+        uint32_t pos[NB];
 #pragma unroll
-        for (uint32_t j = 0; j < BP; j++) {
+        for (uint32_t j = 0; j < NB; j++) {
             if (j < nbp) {
                 const DevBlock blk = a.blocks[b0 + j];
                 const uint32_t r0 = barrett_mod(h0, blk.barrett_m, blk.w);
@@ -207,7 +208,7 @@ __device__ __forceinline__ void row_pass(const TermsArgs &a, const unsigned long
         for (uint32_t i2 = 1; i2 < a.h; i2++) {
             const uint64_t hv = xxh64_u64(code, i2);
 #pragma unroll
-            for (uint32_t j = 0; j < BP; j++) {
+            for (uint32_t j = 0; j < NB; j++) {
                 if (j < nbp) {
                     const DevBlock blk = a.blocks[b0 + j];
                     a.rows_idx[(uint64_t)((b0 + j) * a.h + i2) * a.tcap + base + pos[j]] =
@@ -225,7 +226,17 @@ __device__ __forceinline__ uint64_t windows_of(const TermsArgs &a, uint32_t q, u
     return len >= a.k ? len - a.k + 1 : 0;
 }
 
+// FAST: one hash and at most two blocks (rows at insertion).  The general form
+// runs the row pass TERMS_GENERAL_BP blocks at a time, so every term is hashed
+// once per pass whatever the number of blocks; it is a kernel of its own so its
+// registers do not weigh on the fast form.
+#ifndef COBS_TERMS_GENERAL_BP
+#define COBS_TERMS_GENERAL_BP 8
+#endif
+constexpr uint32_t TERMS_GENERAL_BP = COBS_TERMS_GENERAL_BP;
+template <bool FAST>
 __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
+    constexpr uint32_t NBH = FAST ? 2 : TERMS_GENERAL_BP;  // histograms in shared memory
     extern __shared__ unsigned long long s_table[];
     __shared__ __align__(16) uint8_t s_bytes[TERMS_STAGE_BYTES];
     __shared__ unsigned long long s_list[TERMS_ROUND];  // distinct list of an on-chip set
@@ -233,8 +244,8 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     __shared__ uint16_t s_inv[TERMS_PK_WORDS];  // non-ACGT bytes, 16 per word
     __shared__ uint32_t s_ell;
     __shared__ uint32_t s_has_empty;
-    __shared__ uint32_t s_hist[BP * TERMS_BUCKETS];
-    __shared__ uint32_t s_shift[BP];
+    __shared__ uint32_t s_hist[NBH * TERMS_BUCKETS];
+    __shared__ uint32_t s_shift[NBH];
 
     const uint32_t q = a.q0 + blockIdx.x;
     uint64_t off0;
@@ -252,7 +263,7 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     if (threadIdx.x == 0) { s_ell = 0; s_has_empty = 0; }
 
     // rows at insertion (one hash, at most two blocks): block moduli in shared memory
-    const bool rows_in_list = a.h == 1 && a.n_blocks <= 2;
+    const bool rows_in_list = FAST;
     const uint32_t nb_fast = rows_in_list ? a.n_blocks : 0u;
     __shared__ uint64_t s_fm[2];
     __shared__ uint32_t s_fw[2];
@@ -297,10 +308,11 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
         }
         return;
     }
-    // Blocks are handled BP at a time, so every term is hashed once per pass
-    // whatever the number of blocks.
-    for (uint32_t b0 = 0; b0 < a.n_blocks; b0 += BP)
-        row_pass(a, list, ell, base, b0, a.n_blocks - b0 < BP ? a.n_blocks - b0 : BP, s_hist, s_shift);
+    if constexpr (!FAST) {
+        constexpr uint32_t G = TERMS_GENERAL_BP;
+        for (uint32_t b0 = 0; b0 < a.n_blocks; b0 += G)
+            row_pass<G>(a, list, ell, base, b0, a.n_blocks - b0 < G ? a.n_blocks - b0 : G, s_hist, s_shift);
+    }
 }
 
 // Long queries, insertion: one CTA per round (chunk) of a long query.  The
@@ -342,7 +354,7 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_terms_long_rows(TermsArgs a) 
     const unsigned long long *list = a.codes + base;
     const uint32_t ell = a.ell[q];
     if (a.h != 1) {
-        row_pass(a, list, ell, base, b0, nbp, s_hist, s_shift);
+        row_pass<BP>(a, list, ell, base, b0, nbp, s_hist, s_shift);
         return;
     }
     // bucket counts of every block of the group, then global offsets
@@ -419,13 +431,16 @@ void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s) 
     if (n_queries == 0) return;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_query_terms, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_query_terms<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(TERMS_SMEM_SLOTS * sizeof(unsigned long long)));
+        cudaFuncSetAttribute(k_query_terms<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(TERMS_SMEM_SLOTS * sizeof(unsigned long long)));
         attr_set = true;
     }
     // shared memory sized to the largest set of the launch that is kept on chip
     const size_t dyn = (size_t)a.smem_slots * sizeof(unsigned long long);
-    k_query_terms<<<n_queries, TERMS_THREADS, dyn, s>>>(a);
+    if (a.h == 1 && a.n_blocks <= 2) k_query_terms<true><<<n_queries, TERMS_THREADS, dyn, s>>>(a);
+    else k_query_terms<false><<<n_queries, TERMS_THREADS, dyn, s>>>(a);
     if (a.n_chunks) {
         k_terms_long_insert<<<a.n_chunks, TERMS_THREADS, 0, s>>>(a);
         const uint32_t groups = (a.n_blocks + BP - 1) / BP;
