@@ -28,7 +28,7 @@ struct TermsArgs {
     const DevBlock *blocks;
     uint32_t n_blocks, h, kind, k;
     uint32_t q0;                   // first query handled by blockIdx.x == 0
-    uint32_t smem_slots;           // sets of up to this many slots live in shared memory (<= TERMS_SMEM_SLOTS)
+    uint32_t smem_slots;           // sets of up to this many slots (<= TERMS_SMEM_SLOTS) and their lists live in shared memory
     // Chunk plan of the long queries (more windows than one round): with
     // n_chunks > 0 every long query is processed by one CTA per round (its set
     // at tables + table_base[q] filled with EMPTY_KEY, ell[q] and long_flag[q]

@@ -237,9 +237,11 @@ constexpr uint32_t TERMS_GENERAL_BP = COBS_TERMS_GENERAL_BP;
 template <bool FAST>
 __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     constexpr uint32_t NBH = FAST ? 2 : TERMS_GENERAL_BP;  // histograms in shared memory
+    // dynamic shared memory: the on-chip set (smem_slots) and its distinct list
+    // (a set of cap <= smem_slots slots holds at most cap / 2 terms)
     extern __shared__ unsigned long long s_table[];
+    unsigned long long *s_list = s_table + a.smem_slots;
     __shared__ __align__(16) uint8_t s_bytes[TERMS_STAGE_BYTES];
-    __shared__ unsigned long long s_list[TERMS_ROUND];  // distinct list of an on-chip set
     __shared__ uint32_t s_pk[TERMS_PK_WORDS];   // 2-bit bases, 16 per word
     __shared__ uint16_t s_inv[TERMS_PK_WORDS];  // non-ACGT bytes, 16 per word
     __shared__ uint32_t s_ell;
@@ -431,14 +433,14 @@ void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s) 
     if (n_queries == 0) return;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_query_terms<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(TERMS_SMEM_SLOTS * sizeof(unsigned long long)));
-        cudaFuncSetAttribute(k_query_terms<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(TERMS_SMEM_SLOTS * sizeof(unsigned long long)));
+        const int most = (int)(TERMS_SMEM_SLOTS * 3 / 2 * sizeof(unsigned long long));
+        cudaFuncSetAttribute(k_query_terms<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        cudaFuncSetAttribute(k_query_terms<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         attr_set = true;
     }
-    // shared memory sized to the largest set of the launch that is kept on chip
-    const size_t dyn = (size_t)a.smem_slots * sizeof(unsigned long long);
+    // shared memory sized to the largest set of the launch that is kept on chip,
+    // plus its list of at most half as many terms
+    const size_t dyn = (size_t)(a.smem_slots + a.smem_slots / 2) * sizeof(unsigned long long);
     if (a.h == 1 && a.n_blocks <= 2) k_query_terms<true><<<n_queries, TERMS_THREADS, dyn, s>>>(a);
     else k_query_terms<false><<<n_queries, TERMS_THREADS, dyn, s>>>(a);
     if (a.n_chunks) {
