@@ -127,9 +127,9 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_record(kernel_src):
+def traffic_record(kernel_srcs):
     """The committed ncu record of the gather kernel on the bench workload (DRAM
-    bytes per launch, L2 figures), or None when the kernel source changed since
+    bytes per launch, L2 figures), or None when the kernel's sources changed since
     the counters were taken."""
     p = os.path.join(ROOT, "profiles", "gather_batched_cfg2_dram.txt")
     if not os.path.exists(p):
@@ -139,8 +139,11 @@ def traffic_record(kernel_src):
         if "=" in ln and not ln.startswith("#"):
             k, v = ln.split("=", 1)
             kv[k.strip()] = v.strip()
-    digest = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
-    if kv.get("gather_cu_sha256_16") != digest:
+    h = hashlib.sha256()
+    for p_src in kernel_srcs:
+        h.update(open(p_src, "rb").read())
+    digest = h.hexdigest()[:16]
+    if kv.get("kernel_sources_sha256_16") != digest:
         return None
     try:
         return {"dram_bytes": float(kv["dram_bytes_per_launch_full"]),
@@ -365,7 +368,8 @@ def run_gpu(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
 
-    eng = cobs.Engine(dix, stream=sh, slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm)
+    eng = cobs.Engine(dix, stream=sh, slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm,
+                     gather_feed=args.gather_feed)
     tuned = None
     if args.autotune:
         tuned = eng.autotune(d_q, d_off, wl.q_off, d_thr)
@@ -430,7 +434,8 @@ def run_gpu(args):
     # pipelined: two engines on two streams alternate submit / download, so one
     # batch's copies and host planning overlap the other's kernels
     stream2 = torch.cuda.Stream()
-    eng2 = cobs.Engine(dix, stream=stream2.cuda_stream, slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm)
+    eng2 = cobs.Engine(dix, stream=stream2.cuda_stream, slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm,
+                     gather_feed=args.gather_feed)
     engs = [eng, eng2]
     n_pipe = max(20, args.e2e_steps)
     for e in engs:  # warm both (graph capture, buffers)
@@ -466,6 +471,7 @@ def run_gpu(args):
     if not args.skip_streamed:
         sdix = cobs.DeviceIndex.load_streamed(dix.download(), device=local)
         seng = cobs.Engine(sdix, stream=sh, slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm,
+                     gather_feed=args.gather_feed,
                            stage_bytes=args.stage_bytes)
         for _ in range(3):
             flush_l2()
@@ -502,7 +508,8 @@ def run_gpu(args):
             parts.append(cobs.DeviceIndex.build(P, wl.docs[int(wl.doc_off[lo]):int(wl.doc_off[hi])], o,
                                                 device=local))
         view = cobs.DeviceIndex.multi(parts)
-        meng = cobs.Engine(view, stream=sh, slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm)
+        meng = cobs.Engine(view, stream=sh, slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm,
+                     gather_feed=args.gather_feed)
         for _ in range(3):
             flush_l2()
             meng.query_device(d_q, d_off, wl.q_off, d_thr, form)
@@ -556,8 +563,10 @@ def run_gpu(args):
     achieved = alg_bytes / (g_ms / 1e3) / 1e9 if g_ms > 0 else None
     # the committed ncu record covers the bench workload (cfg2) in the default
     # launch configuration only
-    default_launch = args.slice_bytes in (0, 128) and args.ctas_per_sm == 0 and not args.autotune
-    rec = traffic_record(os.path.join(ROOT, "paper_1905_09624_gb300", "csrc", "gather.cu")) \
+    default_launch = args.slice_bytes in (0, 128) and args.ctas_per_sm == 0 and not args.autotune \
+        and args.gather_feed == 0
+    csrc = os.path.join(ROOT, "paper_1905_09624_gb300", "csrc")
+    rec = traffic_record([os.path.join(csrc, "gather.cu"), os.path.join(csrc, "gather_common.cuh")]) \
         if args.config == "cfg2" and default_launch else None
     kname = "k_gather_pipe" if wl.num_hashes == 1 else "k_gather_pipe_h" if wl.num_hashes <= 4 else "k_gather_batched"
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
@@ -632,6 +641,7 @@ def main():
     ap.add_argument("--streamed-steps", type=int, default=10, help="timed steps of the streamed and multi-index runs")
     ap.add_argument("--skip-multi", action="store_true", help="skip the multi-index measurement")
     ap.add_argument("--skip-insert", action="store_true", help="skip the incremental-insertion measurement")
+    ap.add_argument("--gather-feed", type=int, default=0, help="0 default, 1 cp.async ring, 2 TMA gather")
     ap.add_argument("--stage-bytes", type=int, default=0, help="streamed index: device staging bytes (0 = 2 slots)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-queries", type=int, default=400)

@@ -242,6 +242,11 @@ typedef struct cobs_engine_cfg {
     uint64_t stage_bytes;     /* streamed index only: device bytes of the staging ring, split
                                  into slots of the largest block's bytes (0 = two slots;
                                  at least one slot, at most one per block) */
+    uint32_t gather_feed;     /* single-hash batched gather at 128-byte slices on a resident
+                                 index: 0 = default, 1 = cp.async ring (16-byte pieces per
+                                 lane), 2 = TMA gather (tile::gather4, four indexed rows per
+                                 copy, one tensor map per block); others use the ring */
+    uint32_t _pad2;
 } cobs_engine_cfg;
 
 cobs_status cobs_engine_create(cobs_device_index *dix, const cobs_engine_cfg *cfg, void *stream,

@@ -58,7 +58,8 @@ class cobs_result(ctypes.Structure):
 class cobs_engine_cfg(ctypes.Structure):
     _fields_ = [("max_queries", ctypes.c_uint64), ("max_query_bytes", ctypes.c_uint64), ("max_hits", ctypes.c_uint64),
                 ("slice_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("l2_hints", ctypes.c_uint32),
-                ("split", ctypes.c_uint32), ("stage_bytes", ctypes.c_uint64)]
+                ("split", ctypes.c_uint32), ("stage_bytes", ctypes.c_uint64), ("gather_feed", ctypes.c_uint32),
+                ("_pad2", ctypes.c_uint32)]
 
 
 class cobs_query_stats(ctypes.Structure):
@@ -356,9 +357,9 @@ class Engine:
     """cobs_engine: reusable query workspace on one device index."""
 
     def __init__(self, dix: DeviceIndex, stream=None, slice_bytes=0, ctas_per_sm=0, max_hits=0, l2_hints=0, split=0,
-                 stage_bytes=0):
+                 stage_bytes=0, gather_feed=0):
         self.dix = dix
-        cfg = cobs_engine_cfg(0, 0, max_hits, slice_bytes, ctas_per_sm, l2_hints, split, stage_bytes)
+        cfg = cobs_engine_cfg(0, 0, max_hits, slice_bytes, ctas_per_sm, l2_hints, split, stage_bytes, gather_feed, 0)
         h = vp()
         check(lib().cobs_engine_create(dix.h, ctypes.byref(cfg), stream, ctypes.byref(h)), "cobs_engine_create")
         self.h = h

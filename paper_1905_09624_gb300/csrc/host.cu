@@ -1,6 +1,8 @@
 // Host runtime and C ABI of the COBS query engine: index planning and device
 // build (Sec. 2.3 "Classic and Compact"), index transfer and files, the query
 // engine with its plain, batched and graph forms, and result assembly.
+#include <cuda.h>  // CUtensorMap and its encoder's types (resolved through the runtime)
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -776,6 +778,48 @@ extern "C" cobs_status cobs_index_load(const char *path, cobs_index **out) {
 
 static const uint32_t MAX_CLASSES = 4;
 
+// Default feed of the single-hash gather at 128-byte slices.
+constexpr bool GATHER_FEED_TMA_DEFAULT = false;
+
+// One tensor map per block for the TMA gather: the block's rows as a 2-D
+// tensor of w rows x rowbytes bytes, copied as boxes of 1 row x 128 bytes (the
+// part of a box past rowbytes reads zeros).  The encoder is the driver's,
+// reached through the runtime.
+static cobs_status make_tensor_maps(cobs_engine *eng) {
+    typedef CUresult (*encode_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static encode_fn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &qr) != cudaSuccess ||
+            qr != cudaDriverEntryPointSuccess || !fn)
+            return set_error(COBS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        encode = (encode_fn)fn;
+    }
+    const cobs_device_index *dix = eng->dix;
+    const size_t nb = dix->blocks.size();
+    std::vector<CUtensorMap> maps(std::max<size_t>(nb, 1));
+    for (size_t b = 0; b < nb; b++) {
+        const cobs_block_info &B = dix->blocks[b];
+        const uint64_t off = dix->dev_row_offset.empty() ? B.row_offset : dix->dev_row_offset[b];
+        void *base = (void *)(dix->dev_rows() + off);
+        const cuuint64_t dims[2] = {B.rowbytes, B.w};
+        const cuuint64_t strides[1] = {B.rowbytes};
+        const cuuint32_t box[2] = {128, 1};
+        const cuuint32_t estr[2] = {1, 1};
+        CUresult r = encode(&maps[b], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return set_error(COBS_ERR_CUDA, "tensor map of block %zu: driver error %d", b, (int)r);
+    }
+    CU(eng->tmaps.ensure(maps.size() * sizeof(CUtensorMap)));
+    CU(cudaMemcpy(eng->tmaps.p, maps.data(), nb * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    return COBS_OK;
+}
+
 static cobs_status ensure_slices(cobs_engine *eng, uint32_t lpq) {
     if (eng->slice_lpq == lpq && eng->n_slices) return COBS_OK;
     std::vector<SliceDesc> sl;
@@ -829,6 +873,21 @@ extern "C" cobs_status cobs_engine_create(cobs_device_index *dix, const cobs_eng
     if (eng->cfg.split > 2) {
         cobs_engine_free(eng);
         return set_error(COBS_ERR_ARG, "split must be 0, 1 or 2");
+    }
+    if (eng->cfg.gather_feed > 2) {
+        cobs_engine_free(eng);
+        return set_error(COBS_ERR_ARG, "gather_feed must be 0, 1 or 2");
+    }
+    {
+        const bool want = eng->cfg.gather_feed == 2 || (eng->cfg.gather_feed == 0 && GATHER_FEED_TMA_DEFAULT);
+        if (want && !dix->streamed && dix->params.num_hashes == 1 && eng->lanes_per_query == 8) {
+            cobs_status ts = make_tensor_maps(eng);
+            if (ts != COBS_OK && eng->cfg.gather_feed == 2) {
+                cobs_engine_free(eng);
+                return ts;
+            }
+            eng->use_tma = ts == COBS_OK;
+        }
     }
     eng->l2_hints = eng->cfg.l2_hints ? eng->cfg.l2_hints : 3;
     eng->hit_cap = eng->cfg.max_hits ? eng->cfg.max_hits : (1ULL << 20);
@@ -1069,7 +1128,7 @@ static cobs_status ensure_buffers(cobs_engine *eng, const BatchPlan &bp) {
     CU(eng->out_scores.ensure(eng->hit_cap * 4));
     CU(eng->scores.ensure(eng->dix->n_docs * 4));
     CU(eng->pin_plan.ensure(plan_bytes(bp) + 64));
-    CU(eng->pin_count.ensure(64));
+    CU(eng->pin_count.ensure(16 * 8));
     return COBS_OK;
 }
 
@@ -1232,6 +1291,8 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
                 ga.l2_row_policy = (eng->l2_hints == 3 || eng->l2_hints == 4) ? 2u : 0u;
                 ga.partials = eng->partials.as<uint16_t>();
                 ga.n_docs = (uint32_t)dix->n_docs;
+                ga.tmaps = eng->use_tma && !dix->streamed ? eng->tmaps.p : nullptr;
+                ga.err = (uint32_t *)(ctr + cobs_engine::ERR_SLOT);
                 if (ga.n_slices == 0 || ga.n_groups == 0) continue;
                 launch_gather_batched_L(ga, eng->lanes_per_query, cl.L, grid, gs(c));
                 eng->stat_launches += 1;
@@ -1318,7 +1379,8 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
     eng->stat_launches += 3;
     CU(cudaGetLastError());
     if (timed) CU(cudaEventRecordWithFlags(eng->ev[3], s, tflag));
-    CU(cudaMemcpyAsync(eng->pin_count.p, ctr, 8, cudaMemcpyDeviceToHost, s));
+    // hit count and the gather's wait-limit flag, read when the batch is collected
+    CU(cudaMemcpyAsync(eng->pin_count.p, ctr, 16 * 8, cudaMemcpyDeviceToHost, s));
     return COBS_OK;
 }
 
@@ -1433,6 +1495,10 @@ cobs_status engine_finish(cobs_engine *eng) {
     if (!eng->pending) return COBS_OK;
     for (int attempt = 0; attempt < 4; attempt++) {
         CU(cudaEventSynchronize(eng->ev_done));
+        if (eng->pin_count.as<uint32_t>()[2 * cobs_engine::ERR_SLOT] != 0) {
+            eng->pending = false;
+            return set_error(COBS_ERR_TIMEOUT, "gather: a bounded wait on a TMA barrier ran out; results invalid");
+        }
         unsigned long long cnt = *eng->pin_count.as<unsigned long long>();
         if (cnt <= eng->hit_cap) {
             eng->pending = false;

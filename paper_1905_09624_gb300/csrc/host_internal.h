@@ -137,6 +137,8 @@ struct cobs_engine {
     cobs::DevBuf plan;                        // term_base | table_base | items | split
     cobs::DevBuf partials;                    // split items: counts per (slot, document)
     cobs::DevBuf long_flag;                   // per query: EMPTY_KEY code seen (long queries)
+    cobs::DevBuf tmaps;                       // TMA gather: one 128-byte tensor map per block
+    bool use_tma = false;
     cobs::DevBuf ell, minsc, qcount, qcursor, hitoff, biglist;
     cobs::DevBuf counters;                    // [0] hit count, [1..] work counters
     cobs::DevBuf rows_idx, tables, codes;
@@ -156,6 +158,7 @@ struct cobs_engine {
     // counter classes of a batch run on their own streams, so a class of a few
     // long queries overlaps the others instead of running alone
     static constexpr int MAX_CLASSES = 4;
+    static constexpr int ERR_SLOT = 14;       // counter slot of the gather's wait-limit flag
     cudaStream_t cls_stream[MAX_CLASSES] = {};
     cudaEvent_t ev_cls[MAX_CLASSES] = {};
     cudaEvent_t ev_terms = nullptr;

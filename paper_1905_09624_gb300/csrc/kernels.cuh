@@ -75,6 +75,10 @@ struct GatherArgs {
     uint32_t l2_row_policy;        // same for the gathered index rows
     uint16_t *partials;            // split items: counts per (partial slot, sorted position)
     uint32_t n_docs;
+    // TMA form (h == 1, 128-byte slices): one 128-byte tensor map per block
+    // (w rows x rowbytes bytes, box 1 x 128), or null for the cp.async ring
+    const void *tmaps;
+    uint32_t *err;                 // set when a bounded wait ran out (results invalid)
 };
 constexpr uint32_t ITEM_WHOLE = 0xFFFFFFFFu;
 // Long queries of small batches are split into items of SPLIT_TERMS terms (a
@@ -104,6 +108,10 @@ void launch_gather_batched_L(const GatherArgs &a, uint32_t lanes_per_query, uint
                              cudaStream_t s);
 uint32_t counter_levels_for(uint32_t max_terms);
 int gather_batched_max_blocks_per_sm(uint32_t lanes_per_query, uint32_t h);
+// the forms launch_gather_batched_L dispatches to (128-byte slices)
+void launch_gather_pipe_h(const GatherArgs &a, uint32_t L, uint32_t grid, cudaStream_t s);  // h = 2..4
+int gather_pipe_h_blocks_per_sm(uint32_t h);
+void launch_gather_tma(const GatherArgs &a, uint32_t L, uint32_t grid, cudaStream_t s);     // h = 1, TMA feed
 // Term arrays: every query's region starts at a multiple of TERM_ALIGN slots and
 // spans a multiple of TERM_ALIGN slots (the gather reads row indices 16 at a time).
 constexpr uint64_t TERM_ALIGN = 16;

@@ -316,3 +316,35 @@ def test_submit_host_pipelined_on_two_engines(compact):
                 engs[i % 2].submit_host(qb, off, thr, flags)
             qs, qb, off, thr = batches[i - 1]
             assert_results_equal(engs[(i - 1) % 2].download(), ref, qs, thr)
+
+
+@pytest.mark.parametrize("feed", [1, 2])
+def test_gather_feeds_agree_with_the_oracle(compact, feed):
+    # the single-hash gather fed by the cp.async ring (1) or by TMA gathers of
+    # four indexed rows per copy (2): identical results, every counter class,
+    # split parts, batched and graph forms, slice remainders of a ragged block
+    wl, ref, dix = compact
+    eng = cobs.Engine(dix, gather_feed=feed)
+    for flags in (cobs.COBS_BATCHED, cobs.COBS_GRAPH):
+        got = eng.query_host(wl.queries, wl.q_off, wl.thresholds, flags)
+        assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
+    lens = synth.lognormal_lengths(97, 80, 30000, 0.4, 25000, 90000)
+    docs, off = synth.dna_docs(97, lens)
+    qb, qo, src = synth.dna_queries(98, 40, docs, off, n_tp=30, median=3000, sigma=1.2, lo=1, hi=30000,
+                                    rate_lo=0.0, rate_hi=0.02)
+    thr = synth.choice_u16(99, 40, [1, 500, 1000])
+    wl2 = synth.Workload("feeds", 0, 31, 1, 0.3, 32, 32, docs, off, qb, qo, thr, src)
+    ref2 = oracle_index(wl2)
+    dix2 = device_index(wl2)
+    for split in (0, 1):
+        eng2 = cobs.Engine(dix2, gather_feed=feed, split=split)
+        got = eng2.query_host(qb, qo, thr, cobs.COBS_BATCHED)
+        assert_results_equal(got, ref2, wl2.query_list(), thr)
+
+
+def test_gather_feed_tma_on_narrow_rows(cfg1):
+    # cfg1: one classic block of 64 documents, 16-byte rows inside 128-byte boxes
+    wl, ref, dix = cfg1
+    eng = cobs.Engine(dix, gather_feed=2)
+    got = eng.query_host(wl.queries, wl.q_off, wl.thresholds, cobs.COBS_BATCHED)
+    assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
