@@ -15,7 +15,10 @@ namespace cobs {
 // carry-save tree reads them.  Every wait on an mbarrier is bounded; a wait
 // that runs out sets the error flag, drains the stages and ends the CTA.
 constexpr int TG_G = 16, TG_D = 2, TG_WARPS = 2, TG_THREADS = TG_WARPS * 32;
-constexpr uint32_t TG_WAIT_POLLS = 1u << 22;
+// A wait suspends the thread for up to TG_SUSPEND_NS per try (the hardware wakes
+// it when the phase completes); TG_WAIT_TRIES tries bound it (about 1.6 s).
+constexpr uint32_t TG_WAIT_TRIES = 1u << 14;
+constexpr uint32_t TG_SUSPEND_NS = 100000;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
@@ -27,16 +30,16 @@ __device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, uint32_t bytes
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(TG_SUSPEND_NS)
         : "memory");
     return ok != 0;
 }
 // Bounded wait of every lane of the warp; false (on all lanes) if any gave up.
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity) {
     bool ok = false;
-    for (uint32_t i = 0; i < TG_WAIT_POLLS && !ok; i++) ok = mbar_try_wait(bar, parity);
+    for (uint32_t i = 0; i < TG_WAIT_TRIES && !ok; i++) ok = mbar_try_wait(bar, parity);
     return __all_sync(FULL, ok);
 }
 __device__ __forceinline__ void tma_gather4(void *dst, const void *tmap, int x, const int (&r)[4], uint64_t *bar,
