@@ -433,7 +433,9 @@ def run_gpu(args):
     e2e_sync_value = terms_total / args.steps / float(np.mean(e2e_times))
     # pipelined: two engines on two streams alternate submit / download, so one
     # batch's copies and host planning overlap the other's kernels
-    stream2 = torch.cuda.Stream()
+    # the second engine on its own stream, or on the first engine's stream (its
+    # kernels then queue behind the first batch's instead of sharing the GPU)
+    stream2 = torch.cuda.Stream() if args.e2e_streams == 2 else stream
     eng2 = cobs.Engine(dix, stream=stream2.cuda_stream, slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm,
                      gather_feed=args.gather_feed)
     engs = [eng, eng2]
@@ -591,7 +593,7 @@ def run_gpu(args):
            "roofline": roofline,
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "ms_per_step": 1e3 * pipe_s, "steps": n_pipe,
-                   "mode": "two engines on two streams alternating cobs_engine_submit_host / cobs_engine_download "
+                   "mode": f"two engines on {args.e2e_streams} stream(s) alternating cobs_engine_submit_host / cobs_engine_download "
                            "(pinned query bytes); every step copies its inputs in and its hits out",
                    "one_call_at_a_time": {"value": e2e_sync_value, "ms_per_step": 1e3 * float(np.mean(e2e_times)),
                                           "call": "cobs_engine_query_host"}},
@@ -642,6 +644,8 @@ def main():
     ap.add_argument("--skip-multi", action="store_true", help="skip the multi-index measurement")
     ap.add_argument("--skip-insert", action="store_true", help="skip the incremental-insertion measurement")
     ap.add_argument("--gather-feed", type=int, default=0, help="0 default, 1 cp.async ring, 2 TMA gather")
+    ap.add_argument("--e2e-streams", type=int, default=2, choices=[1, 2],
+                    help="pipelined end to end: the two engines on two streams or on one")
     ap.add_argument("--stage-bytes", type=int, default=0, help="streamed index: device staging bytes (0 = 2 slots)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-queries", type=int, default=400)
