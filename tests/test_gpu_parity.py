@@ -348,3 +348,30 @@ def test_gather_feed_tma_on_narrow_rows(cfg1):
     eng = cobs.Engine(dix, gather_feed=2)
     got = eng.query_host(wl.queries, wl.q_off, wl.thresholds, cobs.COBS_BATCHED)
     assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
+
+
+def _autotune_and_check(wl, ref, dix):
+    import torch
+    eng = cobs.Engine(dix)
+    dq = torch.from_numpy(wl.queries).cuda()
+    do = torch.from_numpy(wl.q_off.view(np.int64)).cuda()
+    dt = torch.from_numpy(wl.thresholds.view(np.int16)).cuda()
+    cfg = eng.autotune(dq, do, wl.q_off, dt)
+    assert cfg["slice_bytes"] in (32, 64, 128) and cfg["ctas_per_sm"] >= 1 and cfg["l2_hints"] in (1, 2, 3, 4)
+    st = eng.stats()
+    assert (st["slice_bytes"], st["ctas_per_sm"]) == (cfg["slice_bytes"], cfg["ctas_per_sm"])
+    for flags in (cobs.COBS_BATCHED, cobs.COBS_GRAPH):
+        got = eng.query_host(wl.queries, wl.q_off, wl.thresholds, flags)
+        assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
+
+
+def test_autotune_single_hash(compact):
+    # the sweep (slice width x CTAs per SM x L2 hints) ends on one of its shapes
+    # and the engine's results stay those of the oracle
+    wl, ref, dix = compact
+    _autotune_and_check(wl, ref, dix)
+
+
+def test_autotune_three_hashes():
+    wl = synth.config4(n_docs=300, n_q=80, n_words=2000, median=2500, lo=50, hi=20000, block_docs=128)
+    _autotune_and_check(wl, oracle_index(wl), device_index(wl))
