@@ -369,7 +369,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
 
     eng = cobs.Engine(dix, stream=sh, slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm,
-                     gather_feed=args.gather_feed)
+                     gather_feed=args.gather_feed, l2_hints=args.l2_hints)
     tuned = None
     if args.autotune:
         tuned = eng.autotune(d_q, d_off, wl.q_off, d_thr)
@@ -437,7 +437,7 @@ def run_gpu(args):
     # kernels then queue behind the first batch's instead of sharing the GPU)
     stream2 = torch.cuda.Stream() if args.e2e_streams == 2 else stream
     eng2 = cobs.Engine(dix, stream=stream2.cuda_stream, slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm,
-                     gather_feed=args.gather_feed)
+                     gather_feed=args.gather_feed, l2_hints=args.l2_hints)
     engs = [eng, eng2]
     n_pipe = max(20, args.e2e_steps)
     for e in engs:  # warm both (graph capture, buffers)
@@ -473,7 +473,7 @@ def run_gpu(args):
     if not args.skip_streamed:
         sdix = cobs.DeviceIndex.load_streamed(dix.download(), device=local)
         seng = cobs.Engine(sdix, stream=sh, slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm,
-                     gather_feed=args.gather_feed,
+                     gather_feed=args.gather_feed, l2_hints=args.l2_hints,
                            stage_bytes=args.stage_bytes)
         for _ in range(3):
             flush_l2()
@@ -511,7 +511,7 @@ def run_gpu(args):
                                                 device=local))
         view = cobs.DeviceIndex.multi(parts)
         meng = cobs.Engine(view, stream=sh, slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm,
-                     gather_feed=args.gather_feed)
+                     gather_feed=args.gather_feed, l2_hints=args.l2_hints)
         for _ in range(3):
             flush_l2()
             meng.query_device(d_q, d_off, wl.q_off, d_thr, form)
@@ -566,7 +566,7 @@ def run_gpu(args):
     # the committed ncu record covers the bench workload (cfg2) in the default
     # launch configuration only
     default_launch = args.slice_bytes in (0, 128) and args.ctas_per_sm == 0 and not args.autotune \
-        and args.gather_feed == 0
+        and args.gather_feed == 0 and args.l2_hints == 0
     csrc = os.path.join(ROOT, "paper_1905_09624_gb300", "csrc")
     rec = traffic_record([os.path.join(csrc, "gather.cu"), os.path.join(csrc, "gather_common.cuh")]) \
         if args.config == "cfg2" and default_launch else None
@@ -644,6 +644,7 @@ def main():
     ap.add_argument("--skip-multi", action="store_true", help="skip the multi-index measurement")
     ap.add_argument("--skip-insert", action="store_true", help="skip the incremental-insertion measurement")
     ap.add_argument("--gather-feed", type=int, default=0, help="0 default, 1 cp.async ring, 2 TMA gather")
+    ap.add_argument("--l2-hints", type=int, default=0, help="L2 eviction hints of the gather (0 default, 1..4)")
     ap.add_argument("--e2e-streams", type=int, default=2, choices=[1, 2],
                     help="pipelined end to end: the two engines on two streams or on one")
     ap.add_argument("--stage-bytes", type=int, default=0, help="streamed index: device staging bytes (0 = 2 slots)")

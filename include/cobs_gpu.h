@@ -230,7 +230,7 @@ typedef struct cobs_engine_cfg {
     uint32_t slice_bytes;     /* batched row-slice width: 32, 64 or 128; 0 = default (128) */
     uint32_t ctas_per_sm;     /* persistent grid = SMs * ctas_per_sm; 0 = full occupancy */
     uint32_t l2_hints;        /* L2 eviction priority of the batched gather's loads:
-                                 0 = default (3), 1 = none, 2 = row indices evict-first,
+                                 0 = default (4), 1 = none, 2 = row indices evict-first,
                                  3 = row indices evict-first and index rows evict-last,
                                  4 = index rows evict-last */
     uint32_t split;           /* long-query split of the batched form (single-hash indexes):
@@ -302,9 +302,10 @@ typedef struct cobs_query_stats {
 } cobs_query_stats;
 cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out);
 
-/* Autotune the batched kernel's slice width and grid on a sample batch (device
- * inputs as in cobs_engine_query_device); the choice is kept by the engine and
- * cached per index shape.  Writes the chosen values to cfg_out. */
+/* Autotune the batched kernel's slice width, resident CTAs per SM and L2
+ * hints on a sample batch (device inputs as in cobs_engine_query_device): each
+ * shape's gather is timed from a cold L2, best of repeats; the fastest is kept
+ * by the engine.  Writes the chosen values to cfg_out. */
 cobs_status cobs_engine_autotune(cobs_engine *eng, const uint8_t *queries_dev, const uint64_t *offsets_dev,
                                  const uint64_t *offsets_host, const uint16_t *thr_dev, uint64_t n,
                                  cobs_engine_cfg *cfg_out);

@@ -889,7 +889,7 @@ extern "C" cobs_status cobs_engine_create(cobs_device_index *dix, const cobs_eng
             eng->use_tma = ts == COBS_OK;
         }
     }
-    eng->l2_hints = eng->cfg.l2_hints ? eng->cfg.l2_hints : 3;
+    eng->l2_hints = eng->cfg.l2_hints ? eng->cfg.l2_hints : 4;
     eng->hit_cap = eng->cfg.max_hits ? eng->cfg.max_hits : (1ULL << 20);
     for (auto &e : eng->ev) cudaEventCreate(&e);
     cudaEventCreateWithFlags(&eng->ev_done, cudaEventDisableTiming);
@@ -1689,6 +1689,10 @@ extern "C" cobs_status cobs_engine_autotune(cobs_engine *eng, const uint8_t *que
     if (!eng) return set_error(COBS_ERR_ARG, "NULL engine");
     // Sweep slice width x resident CTAs per SM x L2 hints; time the gather phase
     // (CUDA events around the gather kernels), best of the repeats after the first.
+    // Every repeat starts from a cold L2 (a 256 MB write first), as a batch does
+    // whose index rows the previous work has pushed out.
+    DevBuf flush;
+    CU(flush.ensure(256ULL << 20));
     const uint32_t lpqs[3] = {2, 4, 8};
     double best = 1e30;
     uint32_t best_lpq = eng->lanes_per_query, best_cta = eng->ctas_per_sm, best_hint = eng->l2_hints;
@@ -1707,6 +1711,7 @@ extern "C" cobs_status cobs_engine_autotune(cobs_engine *eng, const uint8_t *que
                 eng->l2_hints = n_hints == 1 ? eng->l2_hints : hints_h1[hi];
                 double tbest = 1e30;
                 for (int rep = 0; rep < 3; rep++) {
+                    CU(cudaMemsetAsync(flush.p, rep, flush.bytes, eng->stream));
                     TRY(engine_query(eng, queries_dev, offsets_dev, offsets_host, thr_dev, n, COBS_BATCHED));
                     TRY(engine_finish(eng));
                     float t = 0;
