@@ -159,14 +159,14 @@ __global__ void __launch_bounds__(PH_THREADS) k_gather_pipe_h(GatherArgs a) {
 // when they are created, before any stream capture).
 template <int H>
 static void pipe_h_prepare() {
-    static bool done = false;
-    if (done) return;
-    constexpr int smem = (int)pipe_h_smem<H>();
-    cudaFuncSetAttribute(k_gather_pipe_h<8, 8, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_gather_pipe_h<8, 12, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_gather_pipe_h<8, 16, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_gather_pipe_h<8, 24, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    done = true;
+    static PerDeviceOnce once;
+    once([] {
+        constexpr int smem = (int)pipe_h_smem<H>();
+        cudaFuncSetAttribute(k_gather_pipe_h<8, 8, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_gather_pipe_h<8, 12, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_gather_pipe_h<8, 16, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_gather_pipe_h<8, 24, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    });
 }
 
 template <int H>

@@ -790,14 +790,15 @@ static cobs_status make_tensor_maps(cobs_engine *eng) {
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
     static encode_fn encode = nullptr;
-    if (!encode) {
+    static std::once_flag looked_up;
+    std::call_once(looked_up, [] {
         void *fn = nullptr;
         cudaDriverEntryPointQueryResult qr;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &qr) != cudaSuccess ||
-            qr != cudaDriverEntryPointSuccess || !fn)
-            return set_error(COBS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-        encode = (encode_fn)fn;
-    }
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &qr) == cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            encode = (encode_fn)fn;
+    });
+    if (!encode) return set_error(COBS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     const cobs_device_index *dix = eng->dix;
     const size_t nb = dix->blocks.size();
     std::vector<CUtensorMap> maps(std::max<size_t>(nb, 1));

@@ -3,9 +3,28 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "device_common.cuh"
 
 namespace cobs {
+
+// Runs f once per device and call site (kernel attributes are set per device);
+// safe from several host threads.
+struct PerDeviceOnce {
+    std::mutex m;
+    uint64_t done = 0;  // bit d: done on device d (devices 0..63)
+    template <class F>
+    void operator()(F f) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::lock_guard<std::mutex> g(m);
+        const uint64_t bit = dev < 64 ? 1ULL << dev : 0;
+        if (bit && (done & bit)) return;
+        f();
+        done |= bit;
+    }
+};
 
 // Query-term table: shared-memory slots per CTA before the set spills to global memory.
 constexpr uint32_t TERMS_SMEM_SLOTS = 4096;   // 32 KB: largest distinct set kept in shared memory

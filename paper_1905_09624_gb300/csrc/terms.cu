@@ -431,13 +431,12 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_terms_long_rows(TermsArgs a) 
 
 void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s) {
     if (n_queries == 0) return;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static PerDeviceOnce once;
+    once([] {
         const int most = (int)(TERMS_SMEM_SLOTS * 3 / 2 * sizeof(unsigned long long));
         cudaFuncSetAttribute(k_query_terms<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         cudaFuncSetAttribute(k_query_terms<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-        attr_set = true;
-    }
+    });
     // shared memory sized to the largest set of the launch that is kept on chip,
     // plus its list of at most half as many terms
     const size_t dyn = (size_t)(a.smem_slots + a.smem_slots / 2) * sizeof(unsigned long long);
