@@ -49,7 +49,8 @@ typedef enum {
     COBS_ERR_BUDGET = -5,    /* serve: request can never fit the score-buffer budget */
     COBS_ERR_FORMAT = -6,    /* index file is not a cobs_gpu index or is truncated */
     COBS_ERR_OVERFLOW = -7,  /* a query has more terms than the score width can count */
-    COBS_ERR_NOT_FOUND = -8  /* serve: unknown or already released ticket */
+    COBS_ERR_NOT_FOUND = -8, /* serve: unknown or already released ticket */
+    COBS_ERR_CANCELLED = -9  /* serve: the ticket was cancelled (cobs_serve_cancel) */
 } cobs_status;
 
 /* Index parameters (Sec. 2.1-2.3). */
@@ -325,16 +326,24 @@ typedef struct cobs_serve_stats {
     double p50_ms, p99_ms, max_ms, qps, seconds;  /* latency: submit to result visible to poll */
     double mean_wave_queries;                     /* queries per wave */
     double mean_wave_ms, max_wave_ms;             /* wave launch to its results collected */
+    uint64_t cancelled;                           /* tickets cancelled before their result was read */
+    uint64_t failed;                              /* tickets that ended with an error status */
 } cobs_serve_stats;
 
 /* Start a serve loop on a device index (one scheduler thread; waves overlap on the
  * device on separate streams).  submit copies the query; poll returns COBS_PENDING
  * until the result is ready, then fills *out (valid until cobs_hits_release).
- * submit returns BUDGET if the query can never be admitted. */
+ * submit returns BUDGET if the query can never be admitted.  A wave that does not
+ * finish within wait_timeout_ms fails its tickets with COBS_ERR_TIMEOUT.
+ * cancel: a queued ticket is never launched; one already on the device has its
+ * result dropped when its wave ends (its budget returns then).  Either way poll
+ * returns COBS_ERR_CANCELLED until cobs_hits_release; NOT_FOUND for a ticket that
+ * is unknown or released.  A finished ticket's result is dropped the same way. */
 cobs_status cobs_serve_start(cobs_device_index *dix, const cobs_serve_cfg *cfg, cobs_server **out);
 cobs_status cobs_serve_submit(cobs_server *srv, const uint8_t *q, uint64_t len, uint16_t thr_permille,
                               uint64_t *ticket);
 cobs_status cobs_serve_poll(cobs_server *srv, uint64_t ticket, cobs_hits *out);
+cobs_status cobs_serve_cancel(cobs_server *srv, uint64_t ticket);
 void cobs_hits_release(cobs_server *srv, uint64_t ticket);
 cobs_status cobs_serve_stop(cobs_server *srv, cobs_serve_stats *out);
 
@@ -385,6 +394,14 @@ uint64_t cobs_bloom_width(uint32_t h, uint64_t v, double p);
 
 /* Library version string. */
 const char *cobs_version(void);
+
+/* Host-side fault injection for tests (the paper has no counterpart).  After
+ * `after` more successful device or pinned-host allocations by the library, every
+ * allocation fails as if memory were exhausted, until this is called with a
+ * negative value: the calls that needed memory return COBS_ERR_OOM and leave
+ * their objects freeable and usable.  The failing allocation is never attempted,
+ * so nothing reaches the device.  Process-wide; default off. */
+void cobs_debug_fail_alloc(int64_t after);
 
 #ifdef __cplusplus
 }

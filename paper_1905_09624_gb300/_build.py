@@ -1,6 +1,7 @@
 """Compile the CUDA library libcobs_gpu.so for sm_103a (GB300) in-tree.
 
-One translation unit per .cu file, compiled in parallel, linked with the CUDA
+One translation unit per .cu file (and per host-only .cpp file: the error
+status and the serve scheduler), compiled in parallel, linked with the CUDA
 runtime statically.  Output: paper_1905_09624_gb300/_lib/libcobs_gpu.so.
 """
 from __future__ import annotations
@@ -28,7 +29,7 @@ def _nvcc():
 
 
 def _sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
 
 
 def _headers():
@@ -60,7 +61,7 @@ def build(verbose: bool = False, ptxas_verbose: bool = False, extra_flags=()) ->
     if os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == stamp_val:
         return LIB
     os.makedirs(LIBDIR, exist_ok=True)
-    objs = [os.path.join(LIBDIR, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(LIBDIR, os.path.splitext(os.path.basename(s))[0] + ".o") for s in srcs]
 
     def compile_one(src_obj):
         src, obj = src_obj
@@ -77,7 +78,7 @@ def build(verbose: bool = False, ptxas_verbose: bool = False, extra_flags=()) ->
             if log.strip():
                 print(f"== {os.path.basename(s)}\n{log}")
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lpthread"]
+    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

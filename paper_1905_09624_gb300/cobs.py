@@ -23,6 +23,7 @@ COBS_ERR_BUDGET = -5
 COBS_ERR_FORMAT = -6
 COBS_ERR_OVERFLOW = -7
 COBS_ERR_NOT_FOUND = -8
+COBS_ERR_CANCELLED = -9
 
 COBS_PLAIN = 1
 COBS_BATCHED = 2
@@ -81,7 +82,8 @@ class cobs_serve_stats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_uint64), ("waves", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
                 ("qps", ctypes.c_double), ("seconds", ctypes.c_double), ("mean_wave_queries", ctypes.c_double),
-                ("mean_wave_ms", ctypes.c_double), ("max_wave_ms", ctypes.c_double)]
+                ("mean_wave_ms", ctypes.c_double), ("max_wave_ms", ctypes.c_double),
+                ("cancelled", ctypes.c_uint64), ("failed", ctypes.c_uint64)]
 
 
 _PROTOS = {
@@ -123,6 +125,7 @@ _PROTOS = {
     "cobs_serve_start": (ctypes.c_int, [vp, ctypes.POINTER(cobs_serve_cfg), ctypes.POINTER(vp)]),
     "cobs_serve_submit": (ctypes.c_int, [vp, vp, ctypes.c_uint64, ctypes.c_uint16, u64p]),
     "cobs_serve_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(cobs_hits)]),
+    "cobs_serve_cancel": (ctypes.c_int, [vp, ctypes.c_uint64]),
     "cobs_hits_release": (None, [vp, ctypes.c_uint64]),
     "cobs_serve_stop": (ctypes.c_int, [vp, ctypes.POINTER(cobs_serve_stats)]),
     "cobs_query_one_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_uint64, ctypes.c_uint16, vp, vp, vp,
@@ -130,7 +133,12 @@ _PROTOS = {
     "cobs_last_error": (ctypes.c_char_p, []),
     "cobs_bloom_width": (ctypes.c_uint64, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double]),
     "cobs_version": (ctypes.c_char_p, []),
+    "cobs_debug_fail_alloc": (None, [ctypes.c_int64]),
 }
+
+# the serve loop's entry points, also exported by a host-only scheduler build
+SERVE_PROTOS = {k: _PROTOS[k] for k in ("cobs_serve_submit", "cobs_serve_poll", "cobs_serve_cancel",
+                                        "cobs_hits_release", "cobs_serve_stop", "cobs_last_error")}
 
 _lib = None
 
@@ -152,8 +160,9 @@ def lib(build: bool = True):
 
 
 class CobsError(RuntimeError):
-    def __init__(self, status, where):
-        msg = lib().cobs_last_error().decode(errors="replace")
+    def __init__(self, status, where, msg=None):
+        if msg is None:
+            msg = lib().cobs_last_error().decode(errors="replace")
         super().__init__(f"{where}: status {status}: {msg}")
         self.status = status
 
@@ -435,40 +444,60 @@ class Server:
     def __init__(self, dix: DeviceIndex, score_budget_bytes=0, max_inflight_waves=0, max_wave_queries=0,
                  wait_timeout_ms=0):
         self.dix = dix
+        self._L = lib()
         cfg = cobs_serve_cfg(score_budget_bytes, max_inflight_waves, max_wave_queries, wait_timeout_ms, 0)
         h = vp()
-        check(lib().cobs_serve_start(dix.h, ctypes.byref(cfg), ctypes.byref(h)), "cobs_serve_start")
+        check(self._L.cobs_serve_start(dix.h, ctypes.byref(cfg), ctypes.byref(h)), "cobs_serve_start")
         self.h = h
+
+    @classmethod
+    def attach(cls, library, handle):
+        """Wrap a server handle made by another build of the serve entry points
+        (same names and prototypes, e.g. a host-only scheduler build)."""
+        self = cls.__new__(cls)
+        self.dix, self._L, self.h = None, library, handle
+        return self
+
+    def _check(self, st, where):
+        if st != COBS_OK:
+            raise CobsError(st, where, self._L.cobs_last_error().decode(errors="replace"))
 
     def submit(self, q: bytes, thr: int) -> int:
         t = ctypes.c_uint64()
         buf = np.frombuffer(q, dtype=np.uint8) if len(q) else np.zeros(1, np.uint8)
-        check(lib().cobs_serve_submit(self.h, _ptr(buf), len(q), thr, ctypes.byref(t)), "cobs_serve_submit")
+        self._check(self._L.cobs_serve_submit(self.h, _ptr(buf), len(q), thr, ctypes.byref(t)), "cobs_serve_submit")
         return t.value
 
     def poll(self, ticket):
-        """None while pending, else (n_terms, min_score, ids, scores); raises on a failed request."""
+        """None while pending, else (n_terms, min_score, ids, scores) and the ticket
+        is released; raises CobsError (with .status) on a failed or cancelled one."""
         h = cobs_hits()
-        st = lib().cobs_serve_poll(self.h, ticket, ctypes.byref(h))
+        st = self._L.cobs_serve_poll(self.h, ticket, ctypes.byref(h))
         if st == COBS_PENDING:
             return None
-        check(st, "cobs_serve_poll")
+        self._check(st, "cobs_serve_poll")
         n = h.n_hits
         ids = np.ctypeslib.as_array(h.doc_ids, shape=(n,)).copy() if n else np.zeros(0, np.uint32)
         sc = np.ctypeslib.as_array(h.scores, shape=(n,)).copy() if n else np.zeros(0, np.uint32)
-        lib().cobs_hits_release(self.h, ticket)
+        self._L.cobs_hits_release(self.h, ticket)
         return (h.n_terms, h.min_score, ids, sc)
+
+    def cancel(self, ticket):
+        self._check(self._L.cobs_serve_cancel(self.h, ticket), "cobs_serve_cancel")
+
+    def release(self, ticket):
+        self._L.cobs_hits_release(self.h, ticket)
 
     def stop(self):
         st = cobs_serve_stats()
         if getattr(self, "h", None):
-            check(lib().cobs_serve_stop(self.h, ctypes.byref(st)), "cobs_serve_stop")
+            self._check(self._L.cobs_serve_stop(self.h, ctypes.byref(st)), "cobs_serve_stop")
             self.h = None
         return {k: getattr(st, k) for k, _ in cobs_serve_stats._fields_}
 
     def __del__(self):
-        if getattr(self, "h", None) and _lib is not None:
-            _lib.cobs_serve_stop(self.h, None)
+        if getattr(self, "h", None) and getattr(self, "_L", None) is not None:
+            self._L.cobs_serve_stop(self.h, None)
             self.h = None
 
 

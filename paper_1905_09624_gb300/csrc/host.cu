@@ -17,22 +17,6 @@
 
 using namespace cobs;
 
-namespace cobs {
-
-static thread_local std::string g_err;
-
-cobs_status set_error(cobs_status s, const char *fmt, ...) {
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    g_err = buf;
-    return s;
-}
-
-}  // namespace cobs
-
 #define CU(call)                                                                                        \
     do {                                                                                                \
         cudaError_t e_ = (call);                                                                        \
@@ -47,7 +31,6 @@ cobs_status set_error(cobs_status s, const char *fmt, ...) {
         if (s_ != COBS_OK) return s_;     \
     } while (0)
 
-extern "C" const char *cobs_last_error(void) { return g_err.c_str(); }
 extern "C" const char *cobs_version(void) { return "cobs_gpu 0.1 (sm_103a)"; }
 
 // --------------------------------------------------------------- planning
@@ -294,6 +277,7 @@ static cobs_status set_doc_bits(const cobs_params *P, const uint8_t *d_docs, con
 static cobs_status build_impl(const cobs_params *P, const uint8_t *d_docs, const uint64_t *d_off,
                               const uint64_t *h_off, uint64_t n_docs, int device, cudaStream_t s,
                               cobs_device_index **out) {
+    TraceRange tr("cobs.build");
     TRY(check_params(P));
     std::vector<uint64_t> npos, v;
     TRY(count_terms(P, d_docs, d_off, h_off, n_docs, s, npos, v));
@@ -307,7 +291,11 @@ static cobs_status build_impl(const cobs_params *P, const uint8_t *d_docs, const
     cobs_status st = plan_index(*P, v, dix->blocks, dix->perm);
     if (st != COBS_OK) { delete dix; return st; }
     dix->rows_bytes = dix->blocks.empty() ? 0 : dix->blocks.back().row_offset + dix->blocks.back().w * dix->blocks.back().rowbytes;
-    auto fail = [&](cobs_status e) { delete dix; return e; };
+    auto fail = [&](cobs_status e) {
+        cudaStreamSynchronize(s);  // work already queued may still use the buffers
+        delete dix;
+        return e;
+    };
     cudaError_t ce = dix->rows.ensure(dix->rows_bytes);
     if (ce != cudaSuccess) return fail(set_error(COBS_ERR_OOM, "index rows (%llu bytes): %s",
                                                  (unsigned long long)dix->rows_bytes, cudaGetErrorString(ce)));
@@ -401,6 +389,7 @@ extern "C" cobs_status cobs_build(const cobs_params *params, const uint8_t *docs
 // Resident: rows copied to device memory.  Streamed: rows copied to pinned host
 // memory, streamed block by block by the engines.
 static cobs_status load_impl(const cobs_index *ix, int device, void *stream, bool streamed, cobs_device_index **out) {
+    TraceRange tr("cobs.load");
     if (!ix || !out) return set_error(COBS_ERR_ARG, "NULL argument");
     TRY(check_params(&ix->params));
     CU(cudaSetDevice(device));
@@ -630,7 +619,11 @@ extern "C" cobs_status cobs_index_insert(const cobs_index *ix, const uint8_t *do
     tmp.blocks = res->blocks;
     tmp.perm = res->perm;
     tmp.rows_bytes = old_bytes + new_bytes;
-    auto fail = [&](cobs_status e) { delete res; return e; };
+    auto fail = [&](cobs_status e) {
+        cudaStreamSynchronize(s);  // work already queued may still use the buffers
+        delete res;
+        return e;
+    };
     cudaError_t ce = tmp.rows.ensure(tmp.rows_bytes);
     if (ce == cudaSuccess && old_bytes) ce = cudaMemcpyAsync(tmp.rows.p, ix->rows.data(), old_bytes, cudaMemcpyHostToDevice, s);
     if (ce == cudaSuccess && new_bytes) ce = cudaMemsetAsync(tmp.rows.as<uint8_t>() + old_bytes, 0, new_bytes, s);
@@ -830,6 +823,8 @@ static cobs_status ensure_slices(cobs_engine *eng, uint32_t lpq) {
         for (uint32_t off = 0; off < eng->dix->blocks[b].rowbytes; off += S) sl.push_back(SliceDesc{b, off});
         eng->block_slice0.push_back((uint32_t)sl.size());
     }
+    eng->n_slices = 0;  // no table until the new one is in place
+    eng->slice_lpq = 0;
     CU(eng->slices.ensure(std::max<size_t>(sl.size(), 1) * sizeof(SliceDesc)));
     if (!sl.empty())
         CU(cudaMemcpyAsync(eng->slices.p, sl.data(), sl.size() * sizeof(SliceDesc), cudaMemcpyHostToDevice,
@@ -1143,6 +1138,7 @@ static unsigned long long *counters_of(cobs_engine *eng, uint64_t n) {
 // Enqueue the whole query sequence on the engine stream.
 static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint64_t *d_off, const uint16_t *d_thr,
                            uint32_t flags, bool timed) {
+    TraceRange tr("cobs.enqueue");
     cobs_device_index *dix = eng->dix;
     const BatchPlan &bp = eng->bp;
     const uint64_t n = bp.n;
@@ -1437,8 +1433,19 @@ cobs_status engine_query(cobs_engine *eng, const uint8_t *d_bytes, const uint64_
         return set_error(COBS_ERR_ARG, "a streamed index runs the batched or graph form only");
     const auto t_host = std::chrono::steady_clock::now();
     CU(cudaSetDevice(eng->dix->device));
-    TRY(make_plan(eng, h_off, n, flags != COBS_PLAIN, eng->bp));
-    TRY(ensure_buffers(eng, eng->bp));
+    if (eng->pending) {
+        // the previous batch may still read the pinned plan this call refills: wait
+        // for it (its results were never collected and are dropped)
+        CU(cudaEventSynchronize(eng->ev_done));
+        eng->pending = false;
+    }
+    eng->has_results = false;  // until this batch is enqueued in full
+    TRY(ensure_slices(eng, eng->lanes_per_query));  // (re)made if an earlier call failed to make it
+    {
+        TraceRange tr("cobs.plan");
+        TRY(make_plan(eng, h_off, n, flags != COBS_PLAIN, eng->bp));
+        TRY(ensure_buffers(eng, eng->bp));
+    }
     eng->last_bytes = d_bytes;
     eng->last_off = d_off;
     eng->last_thr = d_thr;
@@ -1446,6 +1453,7 @@ cobs_status engine_query(cobs_engine *eng, const uint8_t *d_bytes, const uint64_
     eng->last_flags = flags;
     if (n == 0) {
         eng->pending = false;
+        eng->has_results = true;
         return COBS_OK;
     }
     fill_pinned_plan(eng);
@@ -1487,6 +1495,7 @@ cobs_status engine_query(cobs_engine *eng, const uint8_t *d_bytes, const uint64_
     }
     CU(cudaEventRecord(eng->ev_done, eng->stream));
     eng->pending = true;
+    eng->has_results = true;
     eng->stat_host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host).count();
     return COBS_OK;
 }
@@ -1494,10 +1503,12 @@ cobs_status engine_query(cobs_engine *eng, const uint8_t *d_bytes, const uint64_
 // Wait for the last batch; if its hits overflowed the capacity, grow and re-run.
 cobs_status engine_finish(cobs_engine *eng) {
     if (!eng->pending) return COBS_OK;
+    TraceRange tr("cobs.finish");
     for (int attempt = 0; attempt < 4; attempt++) {
         CU(cudaEventSynchronize(eng->ev_done));
         if (eng->pin_count.as<uint32_t>()[2 * cobs_engine::ERR_SLOT] != 0) {
             eng->pending = false;
+            eng->has_results = false;
             return set_error(COBS_ERR_TIMEOUT, "gather: a bounded wait on a TMA barrier ran out; results invalid");
         }
         unsigned long long cnt = *eng->pin_count.as<unsigned long long>();
@@ -1508,9 +1519,12 @@ cobs_status engine_finish(cobs_engine *eng) {
         uint64_t cap = eng->hit_cap;
         while (cap < cnt) cap *= 2;
         eng->hit_cap = cap;
+        eng->pending = false;
+        eng->has_results = false;  // truncated hits: valid again only once the re-run is enqueued
         TRY(ensure_buffers(eng, eng->bp));
-        uint32_t fl = eng->last_flags;
-        TRY(engine_query(eng, eng->last_bytes, eng->last_off, eng->last_off_host.data(), eng->last_thr, eng->bp.n, fl));
+        const uint32_t fl = eng->last_flags;
+        const std::vector<uint64_t> off = eng->last_off_host;  // engine_query refills last_off_host
+        TRY(engine_query(eng, eng->last_bytes, eng->last_off, off.data(), eng->last_thr, eng->bp.n, fl));
     }
     return set_error(COBS_ERR_CUDA, "hit capacity kept overflowing");
 }
@@ -1528,6 +1542,7 @@ extern "C" cobs_status cobs_engine_results_device(cobs_engine *eng, const uint32
                                                   const uint32_t **hit_ids, const uint32_t **hit_scores) {
     if (!eng) return set_error(COBS_ERR_ARG, "NULL engine");
     TRY(engine_finish(eng));
+    if (!eng->has_results) return set_error(COBS_ERR_ARG, "no results: no batch ran, or the last one failed");
     if (n_terms) *n_terms = eng->ell.as<uint32_t>();
     if (min_score) *min_score = eng->minsc.as<uint32_t>();
     if (hit_offsets) *hit_offsets = eng->hitoff.as<uint64_t>();
@@ -1547,6 +1562,7 @@ struct ResultStore {
 extern "C" cobs_status cobs_engine_download(cobs_engine *eng, cobs_result **out) {
     if (!eng || !out) return set_error(COBS_ERR_ARG, "NULL argument");
     TRY(engine_finish(eng));
+    if (!eng->has_results) return set_error(COBS_ERR_ARG, "no results: no batch ran, or the last one failed");
     const uint64_t n = eng->bp.n;
     ResultStore *rs = new ResultStore();
     std::vector<uint32_t> ell(n), mn(n);
@@ -1654,6 +1670,7 @@ extern "C" cobs_status cobs_query_batch(cobs_device_index *dix, const uint8_t *q
 extern "C" cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out) {
     if (!eng || !out) return set_error(COBS_ERR_ARG, "NULL argument");
     TRY(engine_finish(eng));
+    if (!eng->has_results) return set_error(COBS_ERR_ARG, "no statistics: no batch ran, or the last one failed");
     memset(out, 0, sizeof *out);
     float t = 0;
     if (eng->bp.n) {  // batched and graph forms: phase events; plain: ev[1] after the last terms launch
@@ -1697,6 +1714,14 @@ extern "C" cobs_status cobs_engine_autotune(cobs_engine *eng, const uint8_t *que
     const uint32_t lpqs[3] = {2, 4, 8};
     double best = 1e30;
     uint32_t best_lpq = eng->lanes_per_query, best_cta = eng->ctas_per_sm, best_hint = eng->l2_hints;
+    // on a failure the engine keeps the shape it had
+    const uint32_t old_lpq = best_lpq, old_cta = best_cta, old_hint = best_hint;
+    auto restore = [&](cobs_status st) {
+        eng->lanes_per_query = old_lpq;
+        eng->ctas_per_sm = old_cta;
+        eng->l2_hints = old_hint;
+        return st;
+    };
     const int occ_max = std::max(1, gather_batched_max_blocks_per_sm(8, eng->dix->params.num_hashes));
     std::vector<int> ctas = {occ_max};
     if (occ_max > 1) ctas.push_back(occ_max / 2);
@@ -1704,7 +1729,8 @@ extern "C" cobs_status cobs_engine_autotune(cobs_engine *eng, const uint8_t *que
     const uint32_t hints_h1[4] = {1, 2, 3, 4};
     const int n_hints = eng->dix->params.num_hashes == 1 ? 4 : 1;  // the h > 1 kernel takes no hints
     for (uint32_t lpq : lpqs) {
-        TRY(ensure_slices(eng, lpq));
+        cobs_status st = ensure_slices(eng, lpq);
+        if (st != COBS_OK) return restore(st);
         eng->lanes_per_query = lpq;
         for (int cta : ctas) {
             eng->ctas_per_sm = (uint32_t)cta;
@@ -1712,9 +1738,11 @@ extern "C" cobs_status cobs_engine_autotune(cobs_engine *eng, const uint8_t *que
                 eng->l2_hints = n_hints == 1 ? eng->l2_hints : hints_h1[hi];
                 double tbest = 1e30;
                 for (int rep = 0; rep < 3; rep++) {
-                    CU(cudaMemsetAsync(flush.p, rep, flush.bytes, eng->stream));
-                    TRY(engine_query(eng, queries_dev, offsets_dev, offsets_host, thr_dev, n, COBS_BATCHED));
-                    TRY(engine_finish(eng));
+                    if (cudaMemsetAsync(flush.p, rep, flush.bytes, eng->stream) != cudaSuccess)
+                        return restore(set_error(COBS_ERR_CUDA, "autotune: L2 flush"));
+                    cobs_status st = engine_query(eng, queries_dev, offsets_dev, offsets_host, thr_dev, n, COBS_BATCHED);
+                    if (st == COBS_OK) st = engine_finish(eng);
+                    if (st != COBS_OK) return restore(st);
                     float t = 0;
                     cudaEventElapsedTime(&t, eng->ev[1], eng->ev[2]);
                     if (rep) tbest = std::min(tbest, (double)t);
@@ -1731,7 +1759,8 @@ extern "C" cobs_status cobs_engine_autotune(cobs_engine *eng, const uint8_t *que
             }
         }
     }
-    TRY(ensure_slices(eng, best_lpq));
+    cobs_status st = ensure_slices(eng, best_lpq);
+    if (st != COBS_OK) return restore(st);
     eng->lanes_per_query = best_lpq;
     eng->ctas_per_sm = best_cta;
     eng->l2_hints = best_hint;

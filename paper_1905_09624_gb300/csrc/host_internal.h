@@ -2,6 +2,7 @@
 // runtime and the serve loop.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <string>
@@ -9,10 +10,19 @@
 
 #include "cobs_gpu.h"
 #include "kernels.cuh"
+#include "status.h"
 
 namespace cobs {
 
-cobs_status set_error(cobs_status s, const char *fmt, ...);
+// NVTX range over a host scope: shows planning, enqueueing and waiting on a
+// profiler's timeline (NVTX is header-only; without a tool attached a range
+// costs a few nanoseconds).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // Device allocation that only grows.
 struct DevBuf {
@@ -31,6 +41,7 @@ struct DevBuf {
         if (n == 0) n = 16;
         if (n <= bytes) return cudaSuccess;
         release();
+        if (alloc_injected_failure()) return cudaErrorMemoryAllocation;
         cudaError_t e = cudaMalloc(&p, n);
         if (e == cudaSuccess) bytes = n;
         else p = nullptr;
@@ -56,6 +67,7 @@ struct PinBuf {
         if (n == 0) n = 16;
         if (n <= bytes) return cudaSuccess;
         release();
+        if (alloc_injected_failure()) return cudaErrorMemoryAllocation;
         cudaError_t e = cudaMallocHost(&p, n);
         if (e == cudaSuccess) bytes = n;
         else p = nullptr;
@@ -173,6 +185,7 @@ struct cobs_engine {
     std::vector<uint64_t> last_off_host;
     uint32_t last_flags = 0;
     bool pending = false;
+    bool has_results = false;  // the last batch was enqueued in full (its buffers hold its results)
 
     // CUDA graph of the batched sequence
     cudaGraphExec_t gexec = nullptr;

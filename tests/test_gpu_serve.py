@@ -154,3 +154,28 @@ def test_wave_timeout_fails_its_tickets_and_the_server_recovers():
     assert np.array_equal(got[2], want[0][2]) and np.array_equal(got[3], want[0][3])
     stats = srv.stop()
     assert stats["completed"] >= 1
+
+
+def test_cancel_on_the_device_and_in_the_queue(served):
+    # one slot and one query per wave: the longest query runs while the others
+    # queue; cancelling it (on the device) and a queued one drops exactly those
+    wl, ref, dix = served
+    ql = wl.query_list()
+    order = sorted(range(len(ql)), key=lambda i: -len(ql[i]))[:12]
+    srv = cobs.Server(dix, max_inflight_waves=1, max_wave_queries=1)
+    tickets = [srv.submit(ql[i], int(wl.thresholds[i])) for i in order]
+    srv.cancel(tickets[0])
+    srv.cancel(tickets[5])
+    keep = [k for k in range(len(order)) if k not in (0, 5)]
+    got = _wait(srv, [tickets[k] for k in keep])
+    assert_results_equal(got, ref, [ql[order[k]] for k in keep], [wl.thresholds[order[k]] for k in keep])
+    for k in (0, 5):
+        with pytest.raises(cobs.CobsError) as e:
+            srv.poll(tickets[k])
+        assert e.value.status == cobs.COBS_ERR_CANCELLED
+        srv.release(tickets[k])
+        with pytest.raises(cobs.CobsError) as e:
+            srv.poll(tickets[k])
+        assert e.value.status == cobs.COBS_ERR_NOT_FOUND
+    stats = srv.stop()
+    assert stats["cancelled"] == 2 and stats["completed"] >= len(keep)
