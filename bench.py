@@ -580,6 +580,12 @@ def run_gpu(args):
                 # whose sector lookups are the binding unit (ncu, same workload)
                 "l2_hit_pct": rec["l2_hit_pct"] if rec else None,
                 "l2_sector_lookups_pct_of_peak": rec["l2_sector_lookups_pct_of_peak"] if rec else None}
+    if rec and g_ms > 0:
+        # the DRAM side of the same launch: the ncu traffic over the live launch time
+        dram_gbs = rec["dram_bytes"] / (g_ms / 1e3) / 1e9
+        roofline.update(dram_gbs=dram_gbs, dram_frac=dram_gbs / peak,
+                        binding_unit="L2 sector lookups (logical row bytes reach the SMs through L2; "
+                                     "frac > 1 is that reuse, not skipped work)")
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
