@@ -92,6 +92,103 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_doc_setbits(SetBitsArgs a) {
     }
 }
 
+// ------------------------------------------------- per-document filters
+// Sec. 2.1 builds one Bloom filter per document and Sec. 2.2 stores the filters
+// bit-sliced.  Here a CTA sets the bits of one document's whole filter in shared
+// memory (atomicOr on shared words: no global atomics), staging the document's
+// windows FILTER_TILE at a time, then writes the filter out column-major.
+__global__ void __launch_bounds__(FILTER_THREADS) k_doc_filter(FilterArgs a) {
+    extern __shared__ __align__(16) uint32_t s_filt[];  // pitch_words
+    __shared__ ChunkStage<FILTER_TILE> st;
+    const uint32_t d = a.col_doc[blockIdx.x];
+    const uint64_t len = a.doc_off[d + 1] - a.doc_off[d];
+    const uint64_t npos = len >= a.k ? len - a.k + 1 : 0;
+    for (uint32_t i = threadIdx.x; i < a.pitch_words; i += blockDim.x) s_filt[i] = 0u;
+    __syncthreads();
+    const uint64_t mask = kmer_mask(a.k);
+    const uint8_t *doc = a.docs + a.doc_off[d];
+    for (uint64_t p0 = 0; p0 < npos; p0 += FILTER_TILE) {
+        const uint32_t nwin = (uint32_t)(npos - p0 < FILTER_TILE ? npos - p0 : FILTER_TILE);
+        stage_chunk(st, doc, p0, nwin, a.k, a.kind != KIND_BYTES);  // ends with a barrier
+        for (uint32_t p = threadIdx.x; p < nwin; p += blockDim.x) {
+            uint64_t code;
+            if (!chunk_term(st, p, a.kind, a.k, mask, &code)) continue;
+            for (uint32_t i = 0; i < a.h; i++) {
+                const uint32_t r = barrett_mod(xxh64_u64(code, i), a.barrett_m, a.w);
+                atomicOr(&s_filt[r >> 5], 1u << (r & 31u));
+            }
+        }
+        __syncthreads();  // the stage is refilled next; the last barrier also orders the copy-out
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(a.filters + (uint64_t)blockIdx.x * a.pitch_words);
+    const uint4 *src = reinterpret_cast<const uint4 *>(s_filt);
+    for (uint32_t i = threadIdx.x; i < a.pitch_words / 4; i += blockDim.x) dst[i] = src[i];
+}
+
+// 32 x 32 bit-matrix transpose across a warp: lane l holds row l (bit c =
+// column c); afterwards lane l holds column l (bit c = row c).  Five rounds swap
+// the off-diagonal j x j blocks of every 2j x 2j block with the partner lane
+// l ^ j (the recursive block transpose of Warren, "Hacker's Delight", 2nd ed.,
+// Sec. 7-3, with the rows in lanes instead of an array).
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, uint32_t lane) {
+    uint32_t m = 0x0000FFFFu;
+#pragma unroll
+    for (uint32_t j = 16; j != 0; j >>= 1, m ^= m << j) {
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? ((x & ~m) | ((y >> j) & m)) : ((x & m) | ((y << j) & ~m));
+    }
+    return x;
+}
+
+// Tile of 256 filters (documents c0.., one per thread) x 8 filter words (256
+// rows): each warp turns its 32 documents x 32 rows sub-tiles around (afterwards
+// lane i holds row i of the sub-tile, bit l = document l), then every thread
+// writes one row's 32 bytes (documents c0..c0+255, LSB-first) in two 16-byte
+// stores, the second only if the row is that wide.
+__global__ void __launch_bounds__(TRANSPOSE_DOCS) k_filter_transpose(TransposeArgs a) {
+    __shared__ uint32_t s_in[TRANSPOSE_DOCS][TRANSPOSE_WORDS + 1];       // [document][word]
+    __shared__ uint32_t s_out[TRANSPOSE_WORDS * 32][TRANSPOSE_WORDS + 1];  // [row][32-document word]
+    const uint32_t t = threadIdx.x, warp = t >> 5, lane = t & 31u;
+    const uint32_t wi0 = blockIdx.x * TRANSPOSE_WORDS;
+    const uint32_t c0 = blockIdx.y * TRANSPOSE_DOCS;
+    uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+    if (c0 + t < a.n_cols) {  // documents past the wave: zero bits (padding columns stay zero)
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.filters + (uint64_t)(c0 + t) * a.pitch_words + wi0);
+        lo = src[0];
+        hi = src[1];
+    }
+    s_in[t][0] = lo.x; s_in[t][1] = lo.y; s_in[t][2] = lo.z; s_in[t][3] = lo.w;
+    s_in[t][4] = hi.x; s_in[t][5] = hi.y; s_in[t][6] = hi.z; s_in[t][7] = hi.w;
+    __syncthreads();
+#pragma unroll 1
+    for (uint32_t word = 0; word < TRANSPOSE_WORDS; word++) {
+        s_out[32u * word + lane][warp] = warp_transpose32(s_in[32u * warp + lane][word], lane);
+    }
+    __syncthreads();
+    const uint32_t r = 32u * wi0 + t;
+    const uint32_t byte0 = (a.col0 + c0) / 8u;
+    if (r < a.w && byte0 < a.rowbytes) {
+        uint8_t *dst = a.rows + (uint64_t)r * a.rowbytes + byte0;
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(s_out[t][0], s_out[t][1], s_out[t][2], s_out[t][3]);
+        if (byte0 + 16u < a.rowbytes)
+            *reinterpret_cast<uint4 *>(dst + 16) = make_uint4(s_out[t][4], s_out[t][5], s_out[t][6], s_out[t][7]);
+    }
+}
+
+void launch_doc_filter(const FilterArgs &a, uint32_t n_cols, cudaStream_t s) {
+    static PerDeviceOnce once;
+    once([] {
+        cudaFuncSetAttribute(k_doc_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FILTER_SMEM_MAX);
+    });
+    if (n_cols) k_doc_filter<<<n_cols, FILTER_THREADS, (size_t)a.pitch_words * 4, s>>>(a);
+}
+
+void launch_filter_transpose(const TransposeArgs &a, cudaStream_t s) {
+    if (!a.n_cols) return;
+    const dim3 grid(a.pitch_words / TRANSPOSE_WORDS, (a.n_cols + TRANSPOSE_DOCS - 1) / TRANSPOSE_DOCS);
+    k_filter_transpose<<<grid, TRANSPOSE_DOCS, 0, s>>>(a);
+}
+
 void launch_doc_count(const CountArgs &a, uint32_t n_chunks, cudaStream_t s) {
     if (n_chunks) k_doc_count<<<n_chunks, BUILD_THREADS, 0, s>>>(a);
 }

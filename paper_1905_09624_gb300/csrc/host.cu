@@ -166,10 +166,15 @@ static cobs_status count_terms(const cobs_params *P, const uint8_t *d_docs, cons
         CU(cudaMemsetAsync(dempty.p, 0, n_docs * 4, s));
     }
 
-    // Distinct-term counts, in waves of documents whose sets fit a memory budget.
+    // Distinct-term counts, in waves of documents whose sets fit a budget; every
+    // wave reuses the same set memory.  Build of 10,000 DNA documents (1 GB):
+    // waves of 8 GB 43.8 ms, 512 MB 40.0 ms, 128 MB 43.3 ms, 32 MB 61.1 ms.
+#ifndef COBS_COUNT_WAVE_MB
+#define COBS_COUNT_WAVE_MB 512
+#endif
     size_t free_b = 0, total_b = 0;
     CU(cudaMemGetInfo(&free_b, &total_b));
-    uint64_t budget = std::min<uint64_t>(free_b / 4, 8ULL << 30) / 8;  // in slots
+    uint64_t budget = std::min<uint64_t>(free_b / 4, (uint64_t)COBS_COUNT_WAVE_MB << 20) / 8;  // in slots
     if (budget < (1u << 20)) budget = 1u << 20;
     std::vector<uint64_t> tbase(n_docs);
     std::vector<uint32_t> tcap(n_docs);
@@ -274,6 +279,63 @@ static cobs_status set_doc_bits(const cobs_params *P, const uint8_t *d_docs, con
     return COBS_OK;
 }
 
+// Bloom bits of a freshly planned index (rows zeroed, tables uploaded): blocks
+// whose filter fits in shared memory by per-document filters and a transpose,
+// in waves of whole 256-column tiles whose filters fit a scratch budget; the
+// other blocks by the atomic bit-set.
+static cobs_status set_block_bits(const cobs_params *P, const uint8_t *d_docs, const uint64_t *d_off,
+                                  const std::vector<uint64_t> &npos, cobs_device_index *dix,
+                                  const std::vector<uint32_t> &doc_block, const std::vector<uint32_t> &doc_col,
+                                  cudaStream_t s) {
+    size_t free_b = 0, total_b = 0;
+    CU(cudaMemGetInfo(&free_b, &total_b));
+    const uint64_t budget = std::min<uint64_t>(free_b / 4, 1ULL << 30);
+    std::vector<uint64_t> rest;  // documents of the other blocks, by column
+    DevBuf dfilt;
+    for (uint64_t b = 0; b < dix->blocks.size(); b++) {
+        const cobs_block_info &B = dix->blocks[b];
+        const uint64_t pitch = (B.w + 255) / 256 * 8;  // ceil(w / 32) words, rounded up to 8
+        if (pitch * 4 > FILTER_SMEM_MAX) {
+            for (uint64_t j = 0; j < B.n_docs; j++) rest.push_back(dix->perm[B.doc_begin + j]);
+            continue;
+        }
+        uint64_t C = budget / (pitch * 4) / TRANSPOSE_DOCS * TRANSPOSE_DOCS;
+        if (C < TRANSPOSE_DOCS) C = TRANSPOSE_DOCS;
+        if (C > B.n_docs) C = (B.n_docs + TRANSPOSE_DOCS - 1) / TRANSPOSE_DOCS * TRANSPOSE_DOCS;
+        CU(dfilt.ensure(C * pitch * 4));
+        for (uint64_t c = 0; c < B.n_docs; c += C) {
+            const uint32_t n_cols = (uint32_t)std::min<uint64_t>(C, B.n_docs - c);
+            FilterArgs fa{};
+            fa.docs = d_docs;
+            fa.doc_off = d_off;
+            fa.col_doc = dix->dperm.as<uint32_t>() + B.doc_begin + c;  // column -> original document
+            fa.filters = dfilt.as<uint32_t>();
+            fa.pitch_words = (uint32_t)pitch;
+            fa.w = (uint32_t)B.w;
+            fa.barrett_m = barrett_m_of(B.w);
+            fa.kind = P->term_kind;
+            fa.k = P->q;
+            fa.h = P->num_hashes;
+            launch_doc_filter(fa, n_cols, s);
+            TransposeArgs ta{};
+            ta.filters = dfilt.as<uint32_t>();
+            ta.pitch_words = (uint32_t)pitch;
+            ta.n_cols = n_cols;
+            ta.col0 = (uint32_t)c;
+            ta.w = (uint32_t)B.w;
+            ta.rowbytes = (uint32_t)B.rowbytes;
+            ta.rows = dix->rows.as<uint8_t>() + B.row_offset;
+            launch_filter_transpose(ta, s);
+            CU(cudaGetLastError());
+        }
+    }
+    if (!rest.empty())
+        TRY(set_doc_bits(P, d_docs, d_off, npos, rest, doc_block, doc_col, dix->dblocks.as<DevBlock>(),
+                         dix->rows.as<uint32_t>(), s));
+    CU(cudaStreamSynchronize(s));  // the filter scratch is freed on return
+    return COBS_OK;
+}
+
 static cobs_status build_impl(const cobs_params *P, const uint8_t *d_docs, const uint64_t *d_off,
                               const uint64_t *h_off, uint64_t n_docs, int device, cudaStream_t s,
                               cobs_device_index **out) {
@@ -310,8 +372,7 @@ static cobs_status build_impl(const cobs_params *P, const uint8_t *d_docs, const
             doc_block[d] = (uint32_t)b;
             doc_col[d] = (uint32_t)j;
         }
-    st = set_doc_bits(P, d_docs, d_off, npos, dix->perm, doc_block, doc_col, dix->dblocks.as<DevBlock>(),
-                      dix->rows.as<uint32_t>(), s);
+    st = set_block_bits(P, d_docs, d_off, npos, dix, doc_block, doc_col, s);
     if (st != COBS_OK) return fail(st);
     *out = dix;
     return COBS_OK;

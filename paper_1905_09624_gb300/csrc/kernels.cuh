@@ -225,4 +225,36 @@ struct SetBitsArgs {
 };
 void launch_doc_setbits(const SetBitsArgs &a, uint32_t n_chunks, cudaStream_t s);
 
+// Bit-set by per-document filters: a CTA builds one document's whole filter of
+// w bits in shared memory, writes it out column-major (`pitch_words` 32-bit words
+// per document, a multiple of 8); a transpose turns tiles of 256 documents x 256
+// rows into the row-major rows.  For blocks whose filter fits in shared memory.
+#ifndef COBS_FILTER_THREADS
+#define COBS_FILTER_THREADS 1024
+#endif
+constexpr uint32_t FILTER_THREADS = COBS_FILTER_THREADS;
+constexpr uint32_t FILTER_TILE = 8192;               // windows staged at a time
+constexpr uint32_t FILTER_SMEM_MAX = 212u * 1024u;   // largest filter kept in shared memory (w <= 1,736,704)
+constexpr uint32_t TRANSPOSE_DOCS = 256, TRANSPOSE_WORDS = 8;
+struct FilterArgs {
+    const uint8_t *docs;
+    const uint64_t *doc_off;
+    const uint32_t *col_doc;       // per CTA (column of the wave): original document
+    uint32_t *filters;             // out: [columns of the wave][pitch_words]
+    uint32_t pitch_words;
+    uint32_t w;
+    uint64_t barrett_m;
+    uint32_t kind, k, h;
+};
+void launch_doc_filter(const FilterArgs &a, uint32_t n_cols, cudaStream_t s);
+struct TransposeArgs {
+    const uint32_t *filters;       // [n_cols][pitch_words]
+    uint32_t pitch_words;
+    uint32_t n_cols;               // documents of the wave
+    uint32_t col0;                 // first column of the wave in the block (a multiple of 256)
+    uint32_t w, rowbytes;
+    uint8_t *rows;                 // row 0 of the block
+};
+void launch_filter_transpose(const TransposeArgs &a, cudaStream_t s);
+
 }  // namespace cobs
