@@ -431,27 +431,29 @@ def run_gpu(args):
         # per query: terms, threshold, hit offset; per hit: id, score
         d2h = wl.n_queries * 4 * 2 + (wl.n_queries + 1) * 8 + len(res[3]) * 8
     e2e_sync_value = terms_total / args.steps / float(np.mean(e2e_times))
-    # pipelined: two engines on two streams alternate submit / download, so one
-    # batch's copies and host planning overlap the other's kernels
-    # the second engine on its own stream, or on the first engine's stream (its
-    # kernels then queue behind the first batch's instead of sharing the GPU)
-    stream2 = torch.cuda.Stream() if args.e2e_streams == 2 else stream
-    eng2 = cobs.Engine(dix, stream=stream2.cuda_stream, slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm,
-                     gather_feed=args.gather_feed, l2_hints=args.l2_hints)
-    engs = [eng, eng2]
+    # pipelined: E engines (own streams) take batches in turn, E - 1 batches in
+    # flight, so one batch's copies and host planning overlap the others' kernels;
+    # with --e2e-streams 1 they share the first engine's stream (their kernels
+    # then queue behind each other instead of sharing the GPU)
+    n_eng = max(2, args.e2e_engines)
+    extra = [cobs.Engine(dix, stream=(torch.cuda.Stream() if args.e2e_streams == 2 else stream).cuda_stream,
+                         slice_bytes=args.slice_bytes, ctas_per_sm=args.ctas_per_sm, gather_feed=args.gather_feed,
+                         l2_hints=args.l2_hints) for _ in range(n_eng - 1)]
+    engs = [eng] + extra
     n_pipe = max(20, args.e2e_steps)
-    for e in engs:  # warm both (graph capture, buffers)
+    for e in engs:  # warm all (graph capture, buffers)
         e.submit_host(pin_q, wl.q_off, wl.thresholds, form)
         e.download_arrays()
     t0 = time.perf_counter()
-    engs[0].submit_host(pin_q, wl.q_off, wl.thresholds, form)
-    for i in range(1, n_pipe + 1):
+    for i in range(n_pipe + n_eng - 1):
         if i < n_pipe:
-            engs[i % 2].submit_host(pin_q, wl.q_off, wl.thresholds, form)
-        res = engs[(i - 1) % 2].download_arrays()
+            engs[i % n_eng].submit_host(pin_q, wl.q_off, wl.thresholds, form)
+        j = i - (n_eng - 1)
+        if j >= 0:
+            res = engs[j % n_eng].download_arrays()
     pipe_s = (time.perf_counter() - t0) / n_pipe
     e2e_value = terms_total / args.steps / pipe_s
-    del eng2
+    del extra, engs
 
     # ---- plain form (one query per kernel sequence) on the same batch
     plain = None
@@ -599,7 +601,8 @@ def run_gpu(args):
            "roofline": roofline,
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "ms_per_step": 1e3 * pipe_s, "steps": n_pipe,
-                   "mode": f"two engines on {args.e2e_streams} stream(s) alternating cobs_engine_submit_host / cobs_engine_download "
+                   "mode": f"{n_eng} engines on {args.e2e_streams if args.e2e_streams == 1 else n_eng} stream(s) taking "
+                           "batches in turn with cobs_engine_submit_host / cobs_engine_download "
                            "(pinned query bytes); every step copies its inputs in and its hits out",
                    "one_call_at_a_time": {"value": e2e_sync_value, "ms_per_step": 1e3 * float(np.mean(e2e_times)),
                                           "call": "cobs_engine_query_host"}},
@@ -651,8 +654,10 @@ def main():
     ap.add_argument("--skip-insert", action="store_true", help="skip the incremental-insertion measurement")
     ap.add_argument("--gather-feed", type=int, default=0, help="0 default, 1 cp.async ring, 2 TMA gather")
     ap.add_argument("--l2-hints", type=int, default=0, help="L2 eviction hints of the gather (0 default, 1..4)")
+    ap.add_argument("--e2e-engines", type=int, default=4,
+                    help="engines taking end-to-end batches in turn (batches in flight + 1)")
     ap.add_argument("--e2e-streams", type=int, default=2, choices=[1, 2],
-                    help="pipelined end to end: the two engines on two streams or on one")
+                    help="pipelined end to end: every engine on its own stream (2) or all on one (1)")
     ap.add_argument("--stage-bytes", type=int, default=0, help="streamed index: device staging bytes (0 = 2 slots)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-queries", type=int, default=400)
