@@ -403,6 +403,13 @@ const char *cobs_version(void);
  * so nothing reaches the device.  Process-wide; default off. */
 void cobs_debug_fail_alloc(int64_t after);
 
+/* Test hook (the paper has no counterpart): scratch budget in bytes of the device
+ * build's waves (the distinct-term sets of a wave of documents, the filters of a
+ * wave of 256-column tiles); 0 restores the library's choice.  A small budget
+ * makes a small build run in many waves.  Process-wide; results do not depend
+ * on it. */
+void cobs_debug_build_scratch(uint64_t bytes);
+
 #ifdef __cplusplus
 }
 #endif

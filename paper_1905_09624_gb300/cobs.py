@@ -134,6 +134,7 @@ _PROTOS = {
     "cobs_bloom_width": (ctypes.c_uint64, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double]),
     "cobs_version": (ctypes.c_char_p, []),
     "cobs_debug_fail_alloc": (None, [ctypes.c_int64]),
+    "cobs_debug_build_scratch": (None, [ctypes.c_uint64]),
 }
 
 # the serve loop's entry points, also exported by a host-only scheduler build

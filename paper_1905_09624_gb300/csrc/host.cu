@@ -176,6 +176,7 @@ static cobs_status count_terms(const cobs_params *P, const uint8_t *d_docs, cons
     CU(cudaMemGetInfo(&free_b, &total_b));
     uint64_t budget = std::min<uint64_t>(free_b / 4, (uint64_t)COBS_COUNT_WAVE_MB << 20) / 8;  // in slots
     if (budget < (1u << 20)) budget = 1u << 20;
+    if (build_scratch_override()) budget = std::max<uint64_t>(build_scratch_override() / 8, 16);
     std::vector<uint64_t> tbase(n_docs);
     std::vector<uint32_t> tcap(n_docs);
     struct Wave { uint64_t d0, d1, c0, c1, slots; };
@@ -289,7 +290,7 @@ static cobs_status set_block_bits(const cobs_params *P, const uint8_t *d_docs, c
                                   cudaStream_t s) {
     size_t free_b = 0, total_b = 0;
     CU(cudaMemGetInfo(&free_b, &total_b));
-    const uint64_t budget = std::min<uint64_t>(free_b / 4, 1ULL << 30);
+    const uint64_t budget = build_scratch_override() ? build_scratch_override() : std::min<uint64_t>(free_b / 4, 1ULL << 30);
     std::vector<uint64_t> rest;  // documents of the other blocks, by column
     DevBuf dfilt;
     for (uint64_t b = 0; b < dix->blocks.size(); b++) {

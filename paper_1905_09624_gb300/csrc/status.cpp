@@ -41,3 +41,14 @@ bool alloc_injected_failure() {
 }  // namespace cobs
 
 extern "C" void cobs_debug_fail_alloc(int64_t after) { cobs::g_alloc_left.store(after < 0 ? -1 : after); }
+
+// ------------------------------------------------- build wave budget
+namespace cobs {
+
+static std::atomic<uint64_t> g_build_scratch{0};
+
+uint64_t build_scratch_override() { return g_build_scratch.load(); }
+
+}  // namespace cobs
+
+extern "C" void cobs_debug_build_scratch(uint64_t bytes) { cobs::g_build_scratch.store(bytes); }

@@ -17,3 +17,11 @@ namespace cobs {
 bool alloc_injected_failure();
 
 }  // namespace cobs
+
+namespace cobs {
+
+// cobs_debug_build_scratch: scratch budget of the device build's waves in bytes
+// (0 = the library's choice).
+uint64_t build_scratch_override();
+
+}  // namespace cobs
