@@ -92,6 +92,109 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_doc_setbits(SetBitsArgs a) {
     }
 }
 
+// ------------------------------------------------ partitioned distinct count
+// Scatter: the CTA's windows get their partition (multiply-shift of the high 32
+// bits of mix64 of the term) and a rank within it from shared-memory counters; one
+// global atomic per partition reserves the CTA's run, then every term is written
+// to its slot.  Slots past the partition's capacity are not written: the count
+// pass sees the overflow and the document is recounted with a global set.
+__global__ void __launch_bounds__(PART_THREADS) k_part_scatter(PartArgs a) {
+    __shared__ ChunkStage<COUNT_CHUNK> st;
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    unsigned long long *s_code = reinterpret_cast<unsigned long long *>(s_dyn);  // COUNT_CHUNK
+    uint32_t *s_pr = reinterpret_cast<uint32_t *>(s_code + COUNT_CHUNK);          // partition << 12 | rank
+    uint32_t *s_hist = s_pr + COUNT_CHUNK;                                         // PART_MAX
+    uint32_t *s_base = s_hist + PART_MAX;                                          // PART_MAX
+    const uint32_t d = a.chunk_doc[blockIdx.x];
+    const uint64_t len = a.doc_off[d + 1] - a.doc_off[d];
+    const uint64_t npos = len >= a.k ? len - a.k + 1 : 0;
+    const uint64_t p0 = a.chunk_p0[blockIdx.x];
+    const uint32_t nwin = (uint32_t)(npos - p0 < COUNT_CHUNK ? npos - p0 : COUNT_CHUNK);
+    const uint32_t P = a.n_parts[d];
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) s_hist[i] = 0u;
+    stage_chunk(st, a.docs + a.doc_off[d], p0, nwin, a.k, a.kind != KIND_BYTES);  // barriers order the zeroing
+    const uint64_t mask = kmer_mask(a.k);
+    for (uint32_t w = threadIdx.x; w < nwin; w += blockDim.x) {
+        uint64_t code;
+        uint32_t pr = 0xFFFFFFFFu;
+        if (chunk_term(st, w, a.kind, a.k, mask, &code)) {
+            if (code == EMPTY_KEY) {  // kept out of the sets: a flag per document
+                if (atomicExch(&a.has_empty[d], 1u) == 0u) atomicAdd(&a.v[d], 1ULL);
+            } else {
+                const uint64_t h = mix64(code);
+                const uint32_t part = (uint32_t)(((h >> 32) * (uint64_t)P) >> 32);
+                pr = (part << 12) | atomicAdd(&s_hist[part], 1u);
+                s_code[w] = code;
+            }
+        }
+        s_pr[w] = pr;
+    }
+    __syncthreads();
+    const uint64_t pbase = a.part0[d];
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
+        if (s_hist[i]) s_base[i] = atomicAdd(&a.part_count[pbase + i], s_hist[i]);
+    __syncthreads();
+    const uint32_t cap = a.part_cap[d];
+    unsigned long long *out = a.codes + a.code0[d];
+    for (uint32_t w = threadIdx.x; w < nwin; w += blockDim.x) {
+        const uint32_t pr = s_pr[w];
+        if (pr == 0xFFFFFFFFu) continue;
+        const uint32_t part = pr >> 12;
+        const uint32_t slot = s_base[part] + (pr & 4095u);
+        if (slot < cap) out[(uint64_t)part * cap + slot] = s_code[w];
+    }
+}
+
+// Count: the distinct terms of one partition in a shared-memory open-addressing
+// set (home slot from the low 32 bits of the hash: the high bits chose the
+// partition), added to the document's count once per warp.
+__global__ void __launch_bounds__(PART_THREADS) k_part_count(PartArgs a) {
+    extern __shared__ __align__(16) unsigned long long s_set[];  // PART_SET_SLOTS
+    const uint32_t d = a.part_doc[blockIdx.x];
+    const uint32_t n = a.part_count[blockIdx.x];
+    const uint32_t cap = a.part_cap[d];
+    if (n > cap) {  // the scatter dropped terms: recounted with a global set
+        if (threadIdx.x == 0) atomicExch(&a.overflow[d], 1u);
+        return;
+    }
+    for (uint32_t i = threadIdx.x; i < PART_SET_SLOTS; i += blockDim.x) s_set[i] = EMPTY_KEY;
+    __syncthreads();
+    const unsigned long long *src = a.codes + a.code0[d] + (uint64_t)a.part_idx[blockIdx.x] * cap;
+    uint32_t fresh = 0;
+    for (uint32_t i = threadIdx.x; i < ((n + 31u) & ~31u); i += blockDim.x) {
+        if (i < n) {
+            const unsigned long long key = src[i];
+            const uint64_t h = mix64(key);
+            uint32_t slot = (uint32_t)(((h & 0xFFFFFFFFULL) * PART_SET_SLOTS) >> 32);
+            for (uint32_t probe = 0; probe < PART_SET_SLOTS; probe++) {
+                const unsigned long long old = atomicCAS(&s_set[slot], (unsigned long long)EMPTY_KEY, key);
+                if (old == EMPTY_KEY) {
+                    fresh++;
+                    break;
+                }
+                if (old == key) break;
+                slot = (slot + 1u) & (PART_SET_SLOTS - 1u);
+            }
+        }
+    }
+    fresh = __reduce_add_sync(0xffffffffu, fresh);
+    if ((threadIdx.x & 31u) == 0 && fresh) atomicAdd(&a.v[d], (unsigned long long)fresh);
+}
+
+void launch_part_scatter(const PartArgs &a, uint32_t n_chunks, cudaStream_t s) {
+    constexpr int dyn = (int)(COUNT_CHUNK * 8 + COUNT_CHUNK * 4 + 2 * PART_MAX * 4);
+    static PerDeviceOnce once;
+    once([] { cudaFuncSetAttribute(k_part_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn); });
+    if (n_chunks) k_part_scatter<<<n_chunks, PART_THREADS, dyn, s>>>(a);
+}
+
+void launch_part_count(const PartArgs &a, uint32_t n_parts, cudaStream_t s) {
+    constexpr int dyn = (int)(PART_SET_SLOTS * 8);
+    static PerDeviceOnce once;
+    once([] { cudaFuncSetAttribute(k_part_count, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn); });
+    if (n_parts) k_part_count<<<n_parts, PART_THREADS, dyn, s>>>(a);
+}
+
 // ------------------------------------------------- per-document filters
 // Sec. 2.1 builds one Bloom filter per document and Sec. 2.2 stores the filters
 // bit-sliced.  Here a CTA sets the bits of one document's whole filter in shared

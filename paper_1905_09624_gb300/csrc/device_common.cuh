@@ -44,6 +44,18 @@ __device__ __forceinline__ uint64_t xxh64_u64(uint64_t v, uint64_t seed) {
     return acc;
 }
 
+// A 64-bit mixer for hash sets and partitions that only need well-spread bits
+// (not the method's hash): the finalizer of MurmurHash3 (A. Appleby, public
+// domain), xor-shift / multiply / xor-shift / multiply / xor-shift.
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x ^= x >> 33;
+    x *= 0xFF51AFD7ED558CCDULL;
+    x ^= x >> 33;
+    x *= 0xC4CEB9FE1A85EC53ULL;
+    x ^= x >> 33;
+    return x;
+}
+
 // ------------------------------------------------------------- Barrett
 // x mod w by Barrett reduction (P. Barrett, "Implementing the Rivest Shamir and
 // Adleman public key encryption algorithm on a standard digital signal processor",

@@ -127,74 +127,59 @@ static cobs_status upload_tables(cobs_device_index *dix, cudaStream_t s) {
 
 // ------------------------------------------------------------ device build
 
-// Distinct-term counts v[d] of documents on the device (the sizes of Sec. 2.3,
-// determined before the blocks are planned), and their window counts npos[d].
-static cobs_status count_terms(const cobs_params *P, const uint8_t *d_docs, const uint64_t *d_off,
-                               const uint64_t *h_off, uint64_t n_docs, cudaStream_t s, std::vector<uint64_t> &npos,
-                               std::vector<uint64_t> &v) {
-    if (n_docs >= 0xFFFFFFFFULL) return set_error(COBS_ERR_ARG, "n_docs must be < 2^32");
+// Distinct-term counts of the documents `docs` with one open-addressing set per
+// document in global memory (cleared by a memset), in waves of documents whose
+// sets fit a budget; every wave reuses the same set memory.  Adds to dv.
+static cobs_status count_global(const cobs_params *P, const uint8_t *d_docs, const uint64_t *d_off,
+                                const std::vector<uint64_t> &npos, const std::vector<uint32_t> &docs,
+                                DevBuf &dv, DevBuf &dempty, cudaStream_t s) {
+    if (docs.empty()) return COBS_OK;
+    const uint64_t n_docs = npos.size();
     const uint32_t k = P->q;
-    npos.assign(n_docs, 0);
     std::vector<uint32_t> chunk_doc;
     std::vector<uint64_t> chunk_p0;
-    for (uint64_t d = 0; d < n_docs; d++) {
-        if (h_off[d + 1] < h_off[d]) return set_error(COBS_ERR_ARG, "document offsets decrease at %llu",
-                                                      (unsigned long long)d);
-        uint64_t len = h_off[d + 1] - h_off[d];
-        npos[d] = len >= k ? len - k + 1 : 0;
+    for (uint32_t d : docs)
         for (uint64_t p = 0; p < npos[d]; p += COUNT_CHUNK) {
-            chunk_doc.push_back((uint32_t)d);
+            chunk_doc.push_back(d);
             chunk_p0.push_back(p);
         }
-    }
     const uint64_t n_chunks = chunk_doc.size();
     if (n_chunks > 0x7FFFFFFFULL) return set_error(COBS_ERR_ARG, "documents too large for one build");
-
-    DevBuf dchunk_doc, dchunk_p0, dv, dempty, dtbase, dtcap, dtables;
+    DevBuf dchunk_doc, dchunk_p0, dtbase, dtcap, dtables;
     CU(dchunk_doc.ensure(n_chunks * 4));
     CU(dchunk_p0.ensure(n_chunks * 8));
-    CU(dv.ensure(n_docs * 8));
-    CU(dempty.ensure(n_docs * 4));
     CU(dtbase.ensure(n_docs * 8));
     CU(dtcap.ensure(n_docs * 4));
     if (n_chunks) {
         CU(cudaMemcpyAsync(dchunk_doc.p, chunk_doc.data(), n_chunks * 4, cudaMemcpyHostToDevice, s));
         CU(cudaMemcpyAsync(dchunk_p0.p, chunk_p0.data(), n_chunks * 8, cudaMemcpyHostToDevice, s));
     }
-    if (n_docs) {
-        CU(cudaMemsetAsync(dv.p, 0, n_docs * 8, s));
-        CU(cudaMemsetAsync(dempty.p, 0, n_docs * 4, s));
-    }
-
-    // Distinct-term counts, in waves of documents whose sets fit a budget; every
-    // wave reuses the same set memory.  Build of 10,000 DNA documents (1 GB):
-    // waves of 8 GB 43.8 ms, 512 MB 40.0 ms, 128 MB 43.3 ms, 32 MB 61.1 ms.
-#ifndef COBS_COUNT_WAVE_MB
-#define COBS_COUNT_WAVE_MB 512
-#endif
+    // Build of 10,000 DNA documents (1 GB) with every document here: waves of
+    // 8 GB 43.8 ms, 512 MB 40.0 ms, 128 MB 43.3 ms, 32 MB 61.1 ms.
     size_t free_b = 0, total_b = 0;
     CU(cudaMemGetInfo(&free_b, &total_b));
-    uint64_t budget = std::min<uint64_t>(free_b / 4, (uint64_t)COBS_COUNT_WAVE_MB << 20) / 8;  // in slots
+    uint64_t budget = std::min<uint64_t>(free_b / 4, 512ULL << 20) / 8;  // in slots
     if (budget < (1u << 20)) budget = 1u << 20;
     if (build_scratch_override()) budget = std::max<uint64_t>(build_scratch_override() / 8, 16);
-    std::vector<uint64_t> tbase(n_docs);
-    std::vector<uint32_t> tcap(n_docs);
-    struct Wave { uint64_t d0, d1, c0, c1, slots; };
+    std::vector<uint64_t> tbase(n_docs, 0);
+    std::vector<uint32_t> tcap(n_docs, 0);
+    struct Wave { uint64_t i0, i1, c0, c1, slots; };  // docs[i0, i1), chunks [c0, c1)
     std::vector<Wave> waves;
     {
-        uint64_t d = 0, c = 0;
-        while (d < n_docs) {
-            Wave wv{d, d, c, c, 0};
-            while (d < n_docs) {
-                uint64_t sl = set_slots(npos[d]);
-                if (sl > 0xFFFFFFFFULL) return set_error(COBS_ERR_ARG, "document %llu too long", (unsigned long long)d);
-                if (wv.d1 > wv.d0 && wv.slots + sl > budget) break;
+        uint64_t i = 0, c = 0;
+        while (i < docs.size()) {
+            Wave wv{i, i, c, c, 0};
+            while (i < docs.size()) {
+                const uint32_t d = docs[i];
+                const uint64_t sl = set_slots(npos[d]);
+                if (sl > 0xFFFFFFFFULL) return set_error(COBS_ERR_ARG, "document %u too long", d);
+                if (wv.i1 > wv.i0 && wv.slots + sl > budget) break;
                 tbase[d] = wv.slots;
                 tcap[d] = (uint32_t)sl;
                 wv.slots += sl;
                 while (c < n_chunks && chunk_doc[c] == d) c++;
-                d++;
-                wv.d1 = d;
+                i++;
+                wv.i1 = i;
                 wv.c1 = c;
             }
             waves.push_back(wv);
@@ -203,10 +188,8 @@ static cobs_status count_terms(const cobs_params *P, const uint8_t *d_docs, cons
     uint64_t max_slots = 16;
     for (const Wave &wv : waves) max_slots = std::max(max_slots, wv.slots);
     CU(dtables.ensure(max_slots * 8));
-    if (n_docs) {
-        CU(cudaMemcpyAsync(dtbase.p, tbase.data(), n_docs * 8, cudaMemcpyHostToDevice, s));
-        CU(cudaMemcpyAsync(dtcap.p, tcap.data(), n_docs * 4, cudaMemcpyHostToDevice, s));
-    }
+    CU(cudaMemcpyAsync(dtbase.p, tbase.data(), n_docs * 8, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(dtcap.p, tcap.data(), n_docs * 4, cudaMemcpyHostToDevice, s));
     for (const Wave &wv : waves) {
         CU(cudaMemsetAsync(dtables.p, 0xFF, wv.slots * 8, s));
         CountArgs ca{};
@@ -224,9 +207,165 @@ static cobs_status count_terms(const cobs_params *P, const uint8_t *d_docs, cons
         launch_doc_count(ca, (uint32_t)(wv.c1 - wv.c0), s);
         CU(cudaGetLastError());
     }
-    v.assign(n_docs, 0);
-    if (n_docs) CU(cudaMemcpyAsync(v.data(), dv.p, n_docs * 8, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));  // the staging buffers above are freed on return
+    return COBS_OK;
+}
+
+// Distinct-term counts of the documents `docs` by hash partitions (scatter, then
+// a shared-memory set per partition), in waves whose partitions fit a budget.
+// Adds to dv; returns in `overflowed` the documents whose count is incomplete
+// (a partition got more terms than its capacity) and must come from elsewhere.
+static cobs_status count_partitioned(const cobs_params *P, const uint8_t *d_docs, const uint64_t *d_off,
+                                     const std::vector<uint64_t> &npos, const std::vector<uint32_t> &docs,
+                                     DevBuf &dv, DevBuf &dempty, cudaStream_t s, std::vector<uint32_t> &overflowed) {
+    overflowed.clear();
+    if (docs.empty()) return COBS_OK;
+    const uint64_t n_docs = npos.size();
+    std::vector<uint32_t> n_parts(n_docs, 0), part_cap(n_docs, 0);
+    std::vector<uint64_t> part0(n_docs, 0), code0(n_docs, 0);
+    std::vector<uint32_t> chunk_doc, part_doc, part_idx;
+    std::vector<uint64_t> chunk_p0;
+    size_t free_b = 0, total_b = 0;
+    CU(cudaMemGetInfo(&free_b, &total_b));
+    uint64_t budget = std::min<uint64_t>(free_b / 4, 2ULL << 30);  // bytes of partitions per wave
+    if (build_scratch_override()) budget = build_scratch_override();
+    struct Wave { uint64_t c0, c1, q0, q1, slots; };  // chunks [c0, c1), partitions [q0, q1), term slots
+    std::vector<Wave> waves;
+    Wave wv{0, 0, 0, 0, 0};
+    for (uint32_t d : docs) {
+        const uint64_t np = npos[d];
+        const uint64_t pd = std::max<uint64_t>(1, (np + PART_WINDOWS - 1) / PART_WINDOWS);
+        const uint64_t mean = (np + pd - 1) / pd;
+        // mean + 8 standard deviations of a binomial partition size, + 64
+        const uint64_t cap = mean + 8 * (uint64_t)std::ceil(std::sqrt((double)mean)) + 64;
+        const uint64_t need = pd * cap;
+        if (wv.q1 > wv.q0 && (wv.slots + need) * 8 > budget) {
+            waves.push_back(wv);
+            wv = Wave{wv.c1, wv.c1, wv.q1, wv.q1, 0};
+        }
+        n_parts[d] = (uint32_t)pd;
+        part_cap[d] = (uint32_t)cap;
+        part0[d] = wv.q1 - wv.q0;
+        code0[d] = wv.slots;
+        for (uint64_t p = 0; p < np; p += COUNT_CHUNK) {
+            chunk_doc.push_back(d);
+            chunk_p0.push_back(p);
+        }
+        for (uint32_t i = 0; i < pd; i++) {
+            part_doc.push_back(d);
+            part_idx.push_back(i);
+        }
+        wv.c1 = chunk_doc.size();
+        wv.q1 = part_doc.size();
+        wv.slots += need;
+    }
+    waves.push_back(wv);
+    const uint64_t n_chunks = chunk_doc.size(), n_part = part_doc.size();
+    if (n_chunks > 0x7FFFFFFFULL || n_part > 0x7FFFFFFFULL)
+        return set_error(COBS_ERR_ARG, "documents too large for one build");
+    uint64_t max_slots = 1, max_parts = 1;
+    for (const Wave &w : waves) {
+        max_slots = std::max(max_slots, w.slots);
+        max_parts = std::max(max_parts, w.q1 - w.q0);
+    }
+    DevBuf dchunk_doc, dchunk_p0, dpart_doc, dpart_idx, dn_parts, dpart0, dcap, dcode0, dcount, dcodes, dover;
+    CU(dchunk_doc.ensure(n_chunks * 4));
+    CU(dchunk_p0.ensure(n_chunks * 8));
+    CU(dpart_doc.ensure(n_part * 4));
+    CU(dpart_idx.ensure(n_part * 4));
+    CU(dn_parts.ensure(n_docs * 4));
+    CU(dpart0.ensure(n_docs * 8));
+    CU(dcap.ensure(n_docs * 4));
+    CU(dcode0.ensure(n_docs * 8));
+    CU(dover.ensure(n_docs * 4));
+    CU(dcount.ensure(max_parts * 4));
+    CU(dcodes.ensure(max_slots * 8));
+    if (n_chunks) {
+        CU(cudaMemcpyAsync(dchunk_doc.p, chunk_doc.data(), n_chunks * 4, cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(dchunk_p0.p, chunk_p0.data(), n_chunks * 8, cudaMemcpyHostToDevice, s));
+    }
+    CU(cudaMemcpyAsync(dpart_doc.p, part_doc.data(), n_part * 4, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(dpart_idx.p, part_idx.data(), n_part * 4, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(dn_parts.p, n_parts.data(), n_docs * 4, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(dpart0.p, part0.data(), n_docs * 8, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(dcap.p, part_cap.data(), n_docs * 4, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(dcode0.p, code0.data(), n_docs * 8, cudaMemcpyHostToDevice, s));
+    CU(cudaMemsetAsync(dover.p, 0, n_docs * 4, s));
+    for (const Wave &w : waves) {
+        CU(cudaMemsetAsync(dcount.p, 0, (w.q1 - w.q0) * 4, s));
+        PartArgs pa{};
+        pa.docs = d_docs;
+        pa.doc_off = d_off;
+        pa.chunk_doc = dchunk_doc.as<uint32_t>() + w.c0;
+        pa.chunk_p0 = dchunk_p0.as<uint64_t>() + w.c0;
+        pa.part_doc = dpart_doc.as<uint32_t>() + w.q0;
+        pa.part_idx = dpart_idx.as<uint32_t>() + w.q0;
+        pa.n_parts = dn_parts.as<uint32_t>();
+        pa.part0 = dpart0.as<uint64_t>();
+        pa.part_cap = dcap.as<uint32_t>();
+        pa.code0 = dcode0.as<uint64_t>();
+        pa.part_count = dcount.as<uint32_t>();
+        pa.codes = dcodes.as<unsigned long long>();
+        pa.v = dv.as<unsigned long long>();
+        pa.has_empty = dempty.as<uint32_t>();
+        pa.overflow = dover.as<uint32_t>();
+        pa.kind = P->term_kind;
+        pa.k = P->q;
+        launch_part_scatter(pa, (uint32_t)(w.c1 - w.c0), s);
+        launch_part_count(pa, (uint32_t)(w.q1 - w.q0), s);
+        CU(cudaGetLastError());
+    }
+    std::vector<uint32_t> over(n_docs);
+    CU(cudaMemcpyAsync(over.data(), dover.p, n_docs * 4, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    for (uint32_t d : docs)
+        if (over[d]) overflowed.push_back(d);
+    return COBS_OK;
+}
+
+// Distinct-term counts v[d] of documents on the device (the sizes of Sec. 2.3,
+// determined before the blocks are planned), and their window counts npos[d].
+static cobs_status count_terms(const cobs_params *P, const uint8_t *d_docs, const uint64_t *d_off,
+                               const uint64_t *h_off, uint64_t n_docs, cudaStream_t s, std::vector<uint64_t> &npos,
+                               std::vector<uint64_t> &v) {
+    if (n_docs >= 0xFFFFFFFFULL) return set_error(COBS_ERR_ARG, "n_docs must be < 2^32");
+    const uint32_t k = P->q;
+    npos.assign(n_docs, 0);
+    std::vector<uint32_t> part_docs, global_docs;
+    for (uint64_t d = 0; d < n_docs; d++) {
+        if (h_off[d + 1] < h_off[d]) return set_error(COBS_ERR_ARG, "document offsets decrease at %llu",
+                                                      (unsigned long long)d);
+        const uint64_t len = h_off[d + 1] - h_off[d];
+        npos[d] = len >= k ? len - k + 1 : 0;
+        if (npos[d] == 0) continue;  // no terms: v = 0
+        if ((npos[d] + PART_WINDOWS - 1) / PART_WINDOWS <= PART_MAX) part_docs.push_back((uint32_t)d);
+        else global_docs.push_back((uint32_t)d);
+    }
+    // counts and EMPTY flags of the two methods kept apart: a document counted
+    // again with a global set takes that count
+    DevBuf dv_p, de_p, dv_g, de_g;
+    CU(dv_p.ensure(n_docs * 8));
+    CU(de_p.ensure(n_docs * 4));
+    CU(dv_g.ensure(n_docs * 8));
+    CU(de_g.ensure(n_docs * 4));
+    if (n_docs) {
+        CU(cudaMemsetAsync(dv_p.p, 0, n_docs * 8, s));
+        CU(cudaMemsetAsync(de_p.p, 0, n_docs * 4, s));
+        CU(cudaMemsetAsync(dv_g.p, 0, n_docs * 8, s));
+        CU(cudaMemsetAsync(de_g.p, 0, n_docs * 4, s));
+    }
+    std::vector<uint32_t> overflowed;
+    TRY(count_partitioned(P, d_docs, d_off, npos, part_docs, dv_p, de_p, s, overflowed));
+    global_docs.insert(global_docs.end(), overflowed.begin(), overflowed.end());
+    TRY(count_global(P, d_docs, d_off, npos, global_docs, dv_g, de_g, s));
+    std::vector<uint64_t> vg(n_docs);
+    v.assign(n_docs, 0);
+    if (n_docs) {
+        CU(cudaMemcpyAsync(v.data(), dv_p.p, n_docs * 8, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(vg.data(), dv_g.p, n_docs * 8, cudaMemcpyDeviceToHost, s));
+    }
+    CU(cudaStreamSynchronize(s));
+    for (uint32_t d : global_docs) v[d] = vg[d];
     return COBS_OK;
 }
 

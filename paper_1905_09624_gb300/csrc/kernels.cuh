@@ -212,6 +212,40 @@ struct CountArgs {
 };
 void launch_doc_count(const CountArgs &a, uint32_t n_chunks, cudaStream_t s);
 
+// Distinct counts by hash partitions: every window's term goes to one of P_d
+// partitions of its document by the high bits of its hash (a scatter pass, one
+// CTA per COUNT_CHUNK windows, shared-memory ranks and one global atomic per
+// partition and CTA); then one CTA per partition counts its distinct terms in a
+// shared-memory set.  Documents of more than PART_MAX partitions, and any whose
+// partition overflowed its capacity, are counted with global sets instead.
+#ifndef COBS_PART_SET_SLOTS
+#define COBS_PART_SET_SLOTS 8192
+#endif
+constexpr uint32_t PART_SET_SLOTS = COBS_PART_SET_SLOTS;  // shared-memory set of one partition (8 B a slot)
+constexpr uint32_t PART_WINDOWS = PART_SET_SLOTS * 3 / 8;  // windows per partition (target): load <= 0.44
+constexpr uint32_t PART_MAX = 2048;                        // partitions of a document
+constexpr uint32_t PART_THREADS = 256;
+struct PartArgs {
+    const uint8_t *docs;
+    const uint64_t *doc_off;
+    const uint32_t *chunk_doc;     // scatter: per CTA, document
+    const uint64_t *chunk_p0;      // scatter: per CTA, first window
+    const uint32_t *part_doc;      // count: per CTA (partition of the wave), document
+    const uint32_t *part_idx;      // count: per CTA, partition within the document
+    const uint32_t *n_parts;       // per document: P_d
+    const uint64_t *part0;         // per document: first partition (relative to the wave)
+    const uint32_t *part_cap;      // per document: terms a partition holds
+    const uint64_t *code0;         // per document: first term slot (relative to the wave)
+    uint32_t *part_count;          // per partition of the wave: terms appended (zeroed before)
+    unsigned long long *codes;     // the wave's partitions
+    unsigned long long *v;         // out: distinct terms per document (added to)
+    uint32_t *has_empty;           // per document flag for the EMPTY code (bytes kind)
+    uint32_t *overflow;            // per document: a partition overflowed
+    uint32_t kind, k;
+};
+void launch_part_scatter(const PartArgs &a, uint32_t n_chunks, cudaStream_t s);
+void launch_part_count(const PartArgs &a, uint32_t n_parts, cudaStream_t s);
+
 struct SetBitsArgs {
     const uint8_t *docs;
     const uint64_t *doc_off;

@@ -74,3 +74,36 @@ def test_build_in_many_waves(block_docs):
         assert dix.info()["blocks"][0]["n_docs"] == 700  # one block: three 256-column waves
     got = dix.query(wl.queries, wl.q_off, wl.thresholds, cobs.COBS_BATCHED)
     assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
+
+
+def test_low_entropy_documents_overflow_their_partitions():
+    # byte 2-grams over a 3-letter alphabet: at most 9 distinct terms, so nearly
+    # all windows of a document fall into a few partitions and overflow them;
+    # those documents are counted again with global sets
+    rng = np.random.default_rng(311)
+    lens = rng.integers(1000, 20000, 30).astype(np.uint64)
+    docs = rng.choice(np.frombuffer(b"xyz", np.uint8), int(lens.sum())).astype(np.uint8)
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.uint64)
+    qb, qo = docs[:500].copy(), np.array([0, 200, 500], np.uint64)
+    thr = np.array([500, 1000], np.uint16)
+    wl = synth.Workload("low-entropy", 2, 2, 2, 0.3, 8, 32, docs, off, qb, qo, thr, np.zeros(2, np.int64))
+    ref = oracle_index(wl)
+    dix = cobs.DeviceIndex.build(cobs.make_params(**wl.params()), wl.docs, wl.doc_off)
+    assert_index_equal(dix, ref)
+    got = dix.query(wl.queries, wl.q_off, wl.thresholds, cobs.COBS_BATCHED)
+    assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
+
+
+def test_document_beyond_the_partition_limit():
+    # 7 M windows need more than 2,048 partitions (of 3,072 windows each): this
+    # document's distinct count uses a global set, the others' partitions
+    lens = np.array([500] * 6 + [7_000_030], dtype=np.uint64)
+    docs, off = synth.dna_docs(313, lens)
+    qb, qo, src = synth.dna_queries(314, 6, docs, off, n_tp=6, fixed_len=300, rate_lo=0.0, rate_hi=0.0)
+    thr = np.full(6, 1000, np.uint16)
+    wl = synth.Workload("one-long", 0, 31, 1, 0.3, 4, 32, docs, off, qb, qo, thr, src)
+    ref = oracle_index(wl)
+    dix = cobs.DeviceIndex.build(cobs.make_params(**wl.params()), wl.docs, wl.doc_off)
+    assert_index_equal(dix, ref)
+    got = dix.query(wl.queries, wl.q_off, wl.thresholds, cobs.COBS_BATCHED)
+    assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
