@@ -354,10 +354,14 @@ def run_gpu(args):
             e1.record(stream)
         e1.synchronize()
         build_ms.append(e0.elapsed_time(e1))
-    t0 = time.perf_counter()
-    dix_h2d = cobs.DeviceIndex.build(P, wl.docs, wl.doc_off, device=local)
-    build_h2d_s = time.perf_counter() - t0
-    del dix_h2d, d_docs, d_doff
+    build_h2d = []
+    for rep in range(2):  # best of two, as the device-resident build
+        t0 = time.perf_counter()
+        dix_h2d = cobs.DeviceIndex.build(P, wl.docs, wl.doc_off, device=local)
+        build_h2d.append(time.perf_counter() - t0)
+        del dix_h2d
+    build_h2d_s = min(build_h2d)
+    del d_docs, d_doff
     info = dix.info()
     rows_per_term = sum(b["rowbytes"] for b in info["blocks"]) * wl.num_hashes
 
