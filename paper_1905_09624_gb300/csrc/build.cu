@@ -161,18 +161,27 @@ __global__ void __launch_bounds__(PART_THREADS) k_part_count(PartArgs a) {
     __syncthreads();
     const unsigned long long *src = a.codes + a.code0[d] + (uint64_t)a.part_idx[blockIdx.x] * cap;
     uint32_t fresh = 0;
-    for (uint32_t i = threadIdx.x; i < ((n + 31u) & ~31u); i += blockDim.x) {
-        if (i < n) {
-            const unsigned long long key = src[i];
-            const uint64_t h = mix64(key);
+    // PART_BATCH loads in flight per thread before the first insertion waits on one
+    constexpr uint32_t PART_BATCH = 8;
+    for (uint32_t base = threadIdx.x; base < n; base += blockDim.x * PART_BATCH) {
+        unsigned long long key[PART_BATCH];
+#pragma unroll
+        for (uint32_t j = 0; j < PART_BATCH; j++) {
+            const uint32_t i = base + j * blockDim.x;
+            key[j] = i < n ? src[i] : (unsigned long long)EMPTY_KEY;
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < PART_BATCH; j++) {
+            if (key[j] == EMPTY_KEY) continue;  // past the partition's terms (the set never holds EMPTY)
+            const uint64_t h = mix64(key[j]);
             uint32_t slot = (uint32_t)(((h & 0xFFFFFFFFULL) * PART_SET_SLOTS) >> 32);
             for (uint32_t probe = 0; probe < PART_SET_SLOTS; probe++) {
-                const unsigned long long old = atomicCAS(&s_set[slot], (unsigned long long)EMPTY_KEY, key);
+                const unsigned long long old = atomicCAS(&s_set[slot], (unsigned long long)EMPTY_KEY, key[j]);
                 if (old == EMPTY_KEY) {
                     fresh++;
                     break;
                 }
-                if (old == key) break;
+                if (old == key[j]) break;
                 slot = (slot + 1u) & (PART_SET_SLOTS - 1u);
             }
         }
@@ -209,10 +218,23 @@ __global__ void __launch_bounds__(FILTER_THREADS) k_doc_filter(FilterArgs a) {
     for (uint32_t i = threadIdx.x; i < a.pitch_words; i += blockDim.x) s_filt[i] = 0u;
     __syncthreads();
     const uint64_t mask = kmer_mask(a.k);
+    const bool dna = a.kind != KIND_BYTES;
     const uint8_t *doc = a.docs + a.doc_off[d];
+    // the bytes of the next tile are loaded into registers while this tile's
+    // windows are processed (PRE bytes per thread), then staged
+    constexpr uint32_t PRE = (FILTER_TILE + 32 + FILTER_THREADS - 1) / FILTER_THREADS;
+    if (npos) stage_chunk(st, doc, 0, (uint32_t)(npos < FILTER_TILE ? npos : FILTER_TILE), a.k, dna);
     for (uint64_t p0 = 0; p0 < npos; p0 += FILTER_TILE) {
         const uint32_t nwin = (uint32_t)(npos - p0 < FILTER_TILE ? npos - p0 : FILTER_TILE);
-        stage_chunk(st, doc, p0, nwin, a.k, a.kind != KIND_BYTES);  // ends with a barrier
+        const uint64_t q0 = p0 + FILTER_TILE;
+        const uint32_t nnext = q0 < npos ? (uint32_t)(npos - q0 < FILTER_TILE ? npos - q0 : FILTER_TILE) : 0u;
+        const uint32_t nbytes_next = nnext ? nnext + a.k - 1 : 0u;
+        uint8_t pre[PRE];
+#pragma unroll
+        for (uint32_t j = 0; j < PRE; j++) {
+            const uint32_t i = threadIdx.x + j * FILTER_THREADS;
+            pre[j] = i < nbytes_next ? doc[q0 + i] : (uint8_t)0;
+        }
         for (uint32_t p = threadIdx.x; p < nwin; p += blockDim.x) {
             uint64_t code;
             if (!chunk_term(st, p, a.kind, a.k, mask, &code)) continue;
@@ -222,6 +244,18 @@ __global__ void __launch_bounds__(FILTER_THREADS) k_doc_filter(FilterArgs a) {
             }
         }
         __syncthreads();  // the stage is refilled next; the last barrier also orders the copy-out
+        if (nnext) {
+#pragma unroll
+            for (uint32_t j = 0; j < PRE; j++) {
+                const uint32_t i = threadIdx.x + j * FILTER_THREADS;
+                if (i < nbytes_next) st.bytes[i] = pre[j];
+            }
+            __syncthreads();
+            if (dna) {
+                pack_bases(st.bytes, nbytes_next, st.pk, st.inv);
+                __syncthreads();
+            }
+        }
     }
     uint4 *dst = reinterpret_cast<uint4 *>(a.filters + (uint64_t)blockIdx.x * a.pitch_words);
     const uint4 *src = reinterpret_cast<const uint4 *>(s_filt);
