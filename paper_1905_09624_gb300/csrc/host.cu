@@ -1192,7 +1192,9 @@ static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n
         bp.term_base[q] = bp.tcap;
         bp.tcap += (np + TERM_ALIGN - 1) / TERM_ALIGN * TERM_ALIGN;
         uint64_t sl = set_slots(np);
-        if (sl > TERMS_SMEM_SLOTS) {
+        // a global set for every query whose set does not fit on chip and for
+        // every query of more than one round (chunk CTAs share its set)
+        if (sl > TERMS_SMEM_SLOTS || np > terms_round_windows()) {
             bp.table_base[q] = bp.total_slots;
             bp.total_slots += sl;
         } else {

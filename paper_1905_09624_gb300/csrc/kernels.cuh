@@ -28,7 +28,10 @@ struct PerDeviceOnce {
 
 // Query-term table: shared-memory slots per CTA before the set spills to global memory.
 constexpr uint32_t TERMS_SMEM_SLOTS = 4096;   // 32 KB: largest distinct set kept in shared memory
-constexpr uint32_t TERMS_THREADS = 256;
+#ifndef COBS_TERMS_THREADS
+#define COBS_TERMS_THREADS 256
+#endif
+constexpr uint32_t TERMS_THREADS = COBS_TERMS_THREADS;
 constexpr uint32_t TERMS_SEG = 8;             // windows rolled by one thread per round
 constexpr uint32_t TERMS_BUCKET_BITS = 6;     // terms are emitted in 64 row buckets per block
 constexpr uint32_t TERMS_BUCKETS = 1u << TERMS_BUCKET_BITS;
