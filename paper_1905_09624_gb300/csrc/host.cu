@@ -1295,6 +1295,21 @@ static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n
     return COBS_OK;
 }
 
+// A streamed index is copied and gathered in column units of at most
+// STREAM_UNIT_BYTES of every row (2-D copies: pitch = rowbytes): the gathers of
+// one unit run while the next unit is copied.  Host-to-device 2-D copies of
+// 512-byte rows ran at the full pinned-memory rate (209 GB/s; 256 bytes: 185,
+// 128 bytes: 107).  A multiple of every slice width.
+constexpr uint64_t STREAM_UNIT_BYTES = 512;
+static uint64_t units_of(uint64_t rowbytes) {
+    return rowbytes <= STREAM_UNIT_BYTES ? 1 : (rowbytes + STREAM_UNIT_BYTES - 1) / STREAM_UNIT_BYTES;
+}
+static uint64_t stream_units(const cobs_device_index *dix) {
+    uint64_t n = 0;
+    for (const auto &B : dix->blocks) n += units_of(B.rowbytes);
+    return n;
+}
+
 // Plan upload: term_base[n] | table_base[n] (u64) | items | split queries (uint4)
 // | long queries | chunk queries | chunk first windows (u32).
 static uint64_t plan_bytes(const BatchPlan &bp) {
@@ -1312,7 +1327,7 @@ static cobs_status ensure_buffers(cobs_engine *eng, const BatchPlan &bp) {
     CU(eng->minsc.ensure(n * 4));
     // qcount, then the counters (one memset clears both): [0] hits, [1..14] work
     // counters, [15] big segments, then 4 per block for a streamed index
-    CU(eng->qcount.ensure(n * 4 + (64 + 4 * nb) * 8));
+    CU(eng->qcount.ensure(n * 4 + (64 + 4 * std::max<uint64_t>(nb, stream_units(eng->dix))) * 8));
     CU(eng->qcursor.ensure(n * 4));
     CU(eng->biglist.ensure(n * 4));
     CU(eng->hitoff.ensure((n + 1) * 8));
@@ -1356,7 +1371,7 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
     const uint32_t *chunk_q = long_q + bp.long_q.size();
     const uint32_t *chunk_w0 = chunk_q + bp.chunk_q.size();
     unsigned long long *ctr = counters_of(eng, n);
-    const uint64_t n_ctr = 16 + (dix->streamed ? 4 * dix->blocks.size() : 0);
+    const uint64_t n_ctr = 16 + (dix->streamed ? 4 * stream_units(dix) : 0);
     eng->stat_launches = 0;
     eng->stat_gather_launches = 0;
     eng->stat_tiles = 0;
@@ -1508,23 +1523,38 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
             const uint32_t nb = (uint32_t)dix->blocks.size();
             const uint32_t MC = (uint32_t)cobs_engine::MAX_CLASSES;
             CU(cudaStreamWaitEvent(eng->copy_stream, eng->ev_fork, 0));
+            const uint32_t S = 16u * eng->lanes_per_query;  // slice width
+            uint32_t unit = 0;                                // running unit: its 4 work counters
             for (uint32_t b = 0; b < nb; b++) {
                 const uint32_t slot = b % eng->n_stage;
                 const cobs_block_info &B = dix->blocks[b];
                 const uint64_t bytes = B.w * B.rowbytes;
                 uint8_t *dst = eng->stage.as<uint8_t>() + slot * eng->stage_slot_bytes;
+                const uint8_t *src = dix->host_rows.as<uint8_t>() + B.row_offset;
                 if (b >= eng->n_stage)
                     for (uint32_t c = 0; c < std::max(n_cls, 1u); c++)
                         CU(cudaStreamWaitEvent(eng->copy_stream, eng->ev_free[slot * MC + c], 0));
-                if (bytes)
-                    CU(cudaMemcpyAsync(dst, dix->host_rows.as<uint8_t>() + B.row_offset, bytes,
-                                       cudaMemcpyHostToDevice, eng->copy_stream));
-                CU(cudaEventRecord(eng->ev_up[slot], eng->copy_stream));
-                for (uint32_t c = 0; c < std::max(n_cls, 1u); c++) CU(cudaStreamWaitEvent(gs(c), eng->ev_up[slot], 0));
                 // the kernels add row_offset_b to the rows pointer: shift the slot back by it
                 const uint8_t *rows = (const uint8_t *)((uintptr_t)dst - (uintptr_t)B.row_offset);
-                gather_classes(rows, eng->block_slice0[b], eng->block_slice0[b + 1] - eng->block_slice0[b],
-                               ctr + 16 + 4 * b);
+                const uint64_t nu = units_of(B.rowbytes);
+                for (uint64_t u = 0; u < nu; u++, unit++) {
+                    const uint64_t c0 = u * STREAM_UNIT_BYTES;
+                    const uint64_t width = std::min<uint64_t>(STREAM_UNIT_BYTES, B.rowbytes - c0);
+                    if (nu == 1) {
+                        if (bytes) CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, eng->copy_stream));
+                    } else if (B.w) {
+                        CU(cudaMemcpy2DAsync(dst + c0, B.rowbytes, src + c0, B.rowbytes, width, B.w,
+                                             cudaMemcpyHostToDevice, eng->copy_stream));
+                    }
+                    CU(cudaEventRecord(eng->ev_up[slot], eng->copy_stream));
+                    for (uint32_t c = 0; c < std::max(n_cls, 1u); c++)
+                        CU(cudaStreamWaitEvent(gs(c), eng->ev_up[slot], 0));
+                    // the unit's slices: byte offsets [c0, c0 + width) of the block's rows
+                    const uint32_t s0 = eng->block_slice0[b] + (uint32_t)(c0 / S);
+                    const uint32_t s1 = std::min<uint32_t>(eng->block_slice0[b + 1],
+                                                           eng->block_slice0[b] + (uint32_t)((c0 + width + S - 1) / S));
+                    gather_classes(rows, s0, s1 - s0, ctr + 16 + 4 * unit);
+                }
                 for (uint32_t c = 0; c < std::max(n_cls, 1u); c++)
                     CU(cudaEventRecord(eng->ev_free[slot * MC + c], gs(c)));
                 eng->stat_h2d_index_bytes += bytes;

@@ -78,3 +78,26 @@ def test_streamed_errors(streamed):
     with pytest.raises(cobs.CobsError) as e:
         sdix.query(wl.queries, wl.q_off, wl.thresholds, cobs.COBS_PLAIN)
     assert e.value.status == cobs.COBS_ERR_ARG
+
+
+@pytest.mark.parametrize("slice_bytes", [32, 128])
+@pytest.mark.parametrize("slots", [1, 2])
+def test_streamed_wide_rows_in_column_units(slice_bytes, slots):
+    # blocks of 5,000 and 1,300 documents: rows of 640 and 176 bytes, so the first
+    # block is copied and gathered in two column units (512 + 128 bytes)
+    lens = synth.lognormal_lengths(83, 6300, 400, 0.4, 60, 3000)
+    docs, off = synth.dna_docs(83, lens)
+    qb, qo, src = synth.dna_queries(84, 60, docs, off, n_tp=40, fixed_len=150, rate_lo=0.0, rate_hi=0.02)
+    thr = synth.choice_u16(85, 60, [200, 700, 1000])
+    wl = synth.Workload("wide-rows", 0, 31, 1, 0.3, 5000, 32, docs, off, qb, qo, thr, src)
+    ref = oracle_index(wl)
+    host = device_index(wl).download()
+    sdix = cobs.DeviceIndex.load_streamed(host)
+    info = sdix.info()
+    assert [b["rowbytes"] for b in info["blocks"]] == [640, 176]
+    slot = max(b["w"] * b["rowbytes"] for b in info["blocks"])
+    eng = cobs.Engine(sdix, slice_bytes=slice_bytes, stage_bytes=slots * ((slot + 255) // 256 * 256))
+    for flags in (cobs.COBS_BATCHED, cobs.COBS_GRAPH, cobs.COBS_GRAPH):
+        got = eng.query_host(wl.queries, wl.q_off, wl.thresholds, flags)
+        assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
+        assert eng.stats()["h2d_index_bytes"] == info["rows_bytes"]
