@@ -482,7 +482,10 @@ static cobs_status build_impl(const cobs_params *P, const uint8_t *d_docs, const
     TraceRange tr("cobs.build");
     TRY(check_params(P));
     std::vector<uint64_t> npos, v;
-    TRY(count_terms(P, d_docs, d_off, h_off, n_docs, s, npos, v));
+    {
+        TraceRange tr_count("cobs.build.count");
+        TRY(count_terms(P, d_docs, d_off, h_off, n_docs, s, npos, v));
+    }
 
     // Plan on the host, then set the Bloom bits on the device.
     cobs_device_index *dix = new cobs_device_index();
@@ -512,7 +515,10 @@ static cobs_status build_impl(const cobs_params *P, const uint8_t *d_docs, const
             doc_block[d] = (uint32_t)b;
             doc_col[d] = (uint32_t)j;
         }
-    st = set_block_bits(P, d_docs, d_off, npos, dix, doc_block, doc_col, s);
+    {
+        TraceRange tr_bits("cobs.build.bits");
+        st = set_block_bits(P, d_docs, d_off, npos, dix, doc_block, doc_col, s);
+    }
     if (st != COBS_OK) return fail(st);
     *out = dix;
     return COBS_OK;
@@ -1460,7 +1466,10 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
             ta.n_chunks = (uint32_t)bp.chunk_q.size();
             eng->stat_launches += 2;
         }
-        launch_query_terms(ta, (uint32_t)n, s);
+        {
+            TraceRange tr_terms("cobs.terms");
+            launch_query_terms(ta, (uint32_t)n, s);
+        }
         eng->stat_launches += 1;
         CU(cudaGetLastError());
         if (timed) CU(cudaEventRecordWithFlags(eng->ev[1], s, tflag));
@@ -1515,6 +1524,7 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
                 eng->stat_tiles += (uint64_t)ga.n_slices * ga.n_groups;
             }
         };
+        TraceRange tr_gather("cobs.gather");
         if (!dix->streamed) {
             gather_classes(dix->dev_rows(), 0, eng->n_slices, ctr + 1);  // classes <= 4 < 15
         } else {
@@ -1605,7 +1615,10 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
     ha.out_scores = eng->out_scores.as<uint32_t>();
     ha.big_list = eng->biglist.as<uint32_t>();
     ha.big_count = ctr + 15;  // cleared with the other counters
-    launch_hits_finalize(ha, s);
+    {
+        TraceRange tr_hits("cobs.hits");
+        launch_hits_finalize(ha, s);
+    }
     eng->stat_launches += 3;
     CU(cudaGetLastError());
     if (timed) CU(cudaEventRecordWithFlags(eng->ev[3], s, tflag));
