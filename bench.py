@@ -39,19 +39,11 @@ def _env_int(name, default):
         return default
 
 
-def workload(name):
+def workload(name, path=None):
+    """The named workload of the JSON workload file (synth/workloads.json unless
+    --workloads names another)."""
     import synth
-    if name == "cfg1":
-        return synth.config1()
-    if name == "cfg2":
-        return synth.config2()
-    if name == "cfg3":
-        return synth.config3()
-    if name == "cfg4":
-        return synth.config4()
-    if name == "cfg2-small":
-        return synth.config2(n_docs=2000, n_q=2000)
-    raise ValueError(name)
+    return synth.workload(name, path)
 
 
 def describe(wl, name):
@@ -193,7 +185,7 @@ def run_reference(args):
     rank = _env_int("RANK", 0)
     if rank != 0:
         return 0
-    wl = workload(args.config)
+    wl = workload(args.config, args.workloads)
     import oracle
     ix = oracle.build_index_threaded(oracle.make_params(**wl.params()), wl.docs, wl.doc_off)
     ql = wl.query_list()
@@ -241,7 +233,7 @@ def aggregate_over_ranks(seconds, units, dist=None, device="cpu"):
 
 
 # -------------------------------------------------------------------- serve
-def run_serve(dix, wl, rates, seconds, verify_oracle=None, inflight=3, wave_max=4096):
+def run_serve(dix, wl, rates, seconds, verify_oracle=None, inflight=3, wave_max=4096, workloads=None):
     """Poisson arrivals (cfg5 recipe on the given index) submitted at their
     arrival times from one thread, results polled from another; p50/p99 are the
     library's submit-to-visible latencies.  Optionally checks a seeded 1% sample
@@ -251,7 +243,8 @@ def run_serve(dix, wl, rates, seconds, verify_oracle=None, inflight=3, wave_max=
     out = []
     for rate in rates:
         n = max(50, int(rate * seconds))
-        qb, qo, thr, src, t_arr = synth.config5_queries(wl, n_q=n, rate=rate)
+        params = dict(synth.serving_params("cfg5", workloads), n_q=n, rate=rate)
+        qb, qo, thr, src, t_arr = synth.config5_queries(wl, **params)
         ql = [bytes(qb[int(qo[i]):int(qo[i + 1])]) for i in range(n)]
         srv = cobs.Server(dix, max_inflight_waves=inflight, max_wave_queries=wave_max)
         tickets = [None] * n
@@ -334,7 +327,7 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    wl = workload(args.config)
+    wl = workload(args.config, args.workloads)
     L = cobs.lib()
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
@@ -630,7 +623,8 @@ def run_gpu(args):
         del eng
         rates = [float(r) for r in args.serve_rates.split(",") if r]
         out["serve"] = run_serve(dix, wl, rates, args.serve_seconds, verify_oracle=oracle_ix,
-                                 inflight=args.serve_inflight, wave_max=args.serve_wave_max)
+                                 inflight=args.serve_inflight, wave_max=args.serve_wave_max,
+                                 workloads=args.workloads)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
@@ -658,6 +652,8 @@ def main():
     ap.add_argument("--skip-insert", action="store_true", help="skip the incremental-insertion measurement")
     ap.add_argument("--gather-feed", type=int, default=0, help="0 default, 1 cp.async ring, 2 TMA gather")
     ap.add_argument("--l2-hints", type=int, default=0, help="L2 eviction hints of the gather (0 default, 1..4)")
+    ap.add_argument("--workloads", default=None,
+                    help="JSON file of named workloads (recipe + parameters); default synth/workloads.json")
     ap.add_argument("--e2e-engines", type=int, default=4,
                     help="engines taking end-to-end batches in turn (batches in flight + 1)")
     ap.add_argument("--e2e-streams", type=int, default=2, choices=[1, 2],

@@ -12,6 +12,7 @@ k, query lengths, thresholds).
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 import subprocess
 from dataclasses import dataclass, field
@@ -229,6 +230,38 @@ def config4(seed_docs=1004, seed_q=2004, n_docs=50_000, n_words=200_000, median=
     qb, qo, src = text_queries(seed_q, n_q, docs, off, q_lo, q_hi, 0.02)
     return Workload("cfg4-text-qgram", TERM_BYTES, 8, 3, 0.1, block_docs, 32, docs, off, qb, qo,
                     np.full(n_q, 700, dtype=np.uint16), src)
+
+
+WORKLOADS_JSON = os.path.join(os.path.dirname(os.path.abspath(__file__)), "workloads.json")
+_RECIPES = ("config1", "config2", "config3", "config4")
+
+
+def workload(name: str, path: str | None = None, **overrides) -> Workload:
+    """A workload by name from a JSON file that maps names to a recipe
+    (config1..config4 above) and its parameters; `overrides` replace parameters.
+    The default file, workloads.json beside this module, holds the recipes'
+    default parameters (cfg1..cfg4, cfg2-small) and the serving queries (cfg5)."""
+    with open(path or WORKLOADS_JSON) as f:
+        table = json.load(f)
+    if name not in table:
+        raise ValueError(f"unknown workload {name!r} (known: {', '.join(sorted(table))})")
+    entry = table[name]
+    if entry["recipe"] not in _RECIPES:
+        raise ValueError(f"workload {name!r} is not a document and query set (recipe {entry['recipe']})")
+    params = dict(entry["params"])
+    params.update(overrides)
+    if "thresholds" in params:
+        params["thresholds"] = tuple(params["thresholds"])
+    return globals()[entry["recipe"]](**params)
+
+
+def serving_params(name: str = "cfg5", path: str | None = None) -> dict:
+    """Parameters of the serving-queries recipe (config5_queries) from the JSON file."""
+    with open(path or WORKLOADS_JSON) as f:
+        entry = json.load(f)[name]
+    if entry["recipe"] != "config5_queries":
+        raise ValueError(f"workload {name!r} is not a serving query set")
+    return dict(entry["params"])
 
 
 def config5_queries(wl2: Workload, seed_q=2005, n_q=20_000, q_median=3162.0, q_sigma=1.151, q_lo=100,

@@ -45,3 +45,23 @@ def test_config_shapes():
     w1 = synth.config1()
     assert w1.n_docs == 64 and w1.n_queries == 200 and np.all(np.diff(w1.doc_off) == 5000)
     assert np.sum(w1.src >= 0) == 100 and np.all(w1.thresholds == 800)
+
+
+def test_workload_file_matches_the_recipes():
+    # the JSON workload file holds exactly the recipes' default parameters, and a
+    # workload built from it is the recipe's workload byte for byte
+    import inspect
+    import json
+    table = json.load(open(synth.WORKLOADS_JSON))
+    for name in ("cfg1", "cfg2", "cfg3", "cfg4"):
+        fn = getattr(synth, table[name]["recipe"])
+        defaults = {k: (list(v.default) if isinstance(v.default, tuple) else v.default)
+                    for k, v in inspect.signature(fn).parameters.items()}
+        assert table[name]["params"] == defaults, name
+    sig = inspect.signature(synth.config5_queries)
+    assert synth.serving_params() == {k: v.default for k, v in sig.parameters.items() if k != "wl2"}
+    a, b = synth.workload("cfg1"), synth.config1()
+    assert np.array_equal(a.docs, b.docs) and np.array_equal(a.queries, b.queries)
+    assert np.array_equal(a.thresholds, b.thresholds) and a.params() == b.params()
+    small = synth.workload("cfg1", n_docs=8, n_q=10)
+    assert small.n_docs == 8 and small.n_queries == 10
