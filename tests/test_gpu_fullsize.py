@@ -31,6 +31,18 @@ def test_cfg2_full_size_index_and_sampled_queries():
     got = eng.download()
     sample = np.random.default_rng(2024).choice(wl.n_queries, 120, replace=False).tolist()
     assert_results_equal(got, ref, wl.query_list(), wl.thresholds, which=sample)
+    # the captured graph (the form bench.py times) gives every query's hits exactly
+    batched = eng.download_arrays()
+    for _ in range(2):  # capture, then replay
+        eng.query_device(d_q, d_off, wl.q_off, d_thr, cobs.COBS_GRAPH)
+        graph = eng.download_arrays()
+        assert all(np.array_equal(a, b) for a, b in zip(graph, batched))
+    # and so does the pipelined host path of the end-to-end measurement
+    pin = torch.empty(len(wl.queries), dtype=torch.uint8, pin_memory=True).numpy()
+    pin[:] = wl.queries
+    eng.submit_host(pin, wl.q_off, wl.thresholds, cobs.COBS_GRAPH)
+    host = eng.download_arrays()
+    assert all(np.array_equal(a, b) for a, b in zip(host, batched))
     # every query is a mutated substring of its source document (1% substitutions,
     # each changing at most 31 of about 970 terms): at K = 0.5 nearly all find it
     half = [i for i in range(wl.n_queries) if wl.thresholds[i] == 500]
