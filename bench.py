@@ -140,7 +140,8 @@ def traffic_record(kernel_srcs):
     try:
         return {"dram_bytes": float(kv["dram_bytes_per_launch_full"]),
                 "l2_hit_pct": float(kv["lts_t_sector_hit_rate_pct"]),
-                "l2_sector_lookups_pct_of_peak": float(kv["lts_t_sectors_srcunit_tex_pct_of_peak"])}
+                "l2_sector_lookups_pct_of_peak": float(kv["lts_t_sectors_srcunit_tex_pct_of_peak"]),
+                "slice_bytes": int(kv.get("slice_bytes", "128"))}
     except (KeyError, ValueError):
         return None
 
@@ -564,11 +565,13 @@ def run_gpu(args):
     achieved = alg_bytes / (g_ms / 1e3) / 1e9 if g_ms > 0 else None
     # the committed ncu record covers the bench workload (cfg2) in the default
     # launch configuration only
-    default_launch = args.slice_bytes in (0, 128) and args.ctas_per_sm == 0 and not args.autotune \
+    default_launch = args.slice_bytes == 0 and args.ctas_per_sm == 0 and not args.autotune \
         and args.gather_feed == 0 and args.l2_hints == 0
     csrc = os.path.join(ROOT, "paper_1905_09624_gb300", "csrc")
     rec = traffic_record([os.path.join(csrc, "gather.cu"), os.path.join(csrc, "gather_common.cuh")]) \
         if args.config == "cfg2" and default_launch else None
+    if rec and rec["slice_bytes"] != eng.stats()["slice_bytes"]:
+        rec = None  # taken with another slice width
     kname = "k_gather_pipe" if wl.num_hashes == 1 else "k_gather_pipe_h" if wl.num_hashes <= 4 else "k_gather_batched"
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"

@@ -239,6 +239,7 @@ void launch_gather_batched_L(const GatherArgs &a, uint32_t lanes_per_query, uint
         switch (lanes_per_query) {
             case 2: launch_pipe_L<2>(a, L, grid, s); break;
             case 4: launch_pipe_L<4>(a, L, grid, s); break;
+            case 16: launch_pipe_L<16>(a, L, grid, s); break;
             default: launch_pipe_L<8>(a, L, grid, s); break;
         }
         return;

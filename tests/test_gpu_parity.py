@@ -50,7 +50,7 @@ def test_compact_index_bit_exact(compact):
     assert_index_equal(dix, ref)
 
 
-@pytest.mark.parametrize("slice_bytes", [32, 64, 128])
+@pytest.mark.parametrize("slice_bytes", [32, 64, 128, 256])
 def test_compact_batched_slice_widths(compact, slice_bytes):
     wl, ref, dix = compact
     eng = cobs.Engine(dix, slice_bytes=slice_bytes)
@@ -357,7 +357,8 @@ def _autotune_and_check(wl, ref, dix):
     do = torch.from_numpy(wl.q_off.view(np.int64)).cuda()
     dt = torch.from_numpy(wl.thresholds.view(np.int16)).cuda()
     cfg = eng.autotune(dq, do, wl.q_off, dt)
-    assert cfg["slice_bytes"] in (32, 64, 128) and cfg["ctas_per_sm"] >= 1 and cfg["l2_hints"] in (1, 2, 3, 4)
+    widths = (32, 64, 128, 256) if wl.num_hashes == 1 else (32, 64, 128)
+    assert cfg["slice_bytes"] in widths and cfg["ctas_per_sm"] >= 1 and cfg["l2_hints"] in (1, 2, 3, 4)
     st = eng.stats()
     assert (st["slice_bytes"], st["ctas_per_sm"]) == (cfg["slice_bytes"], cfg["ctas_per_sm"])
     for flags in (cobs.COBS_BATCHED, cobs.COBS_GRAPH):
@@ -375,3 +376,22 @@ def test_autotune_single_hash(compact):
 def test_autotune_three_hashes():
     wl = synth.config4(n_docs=300, n_q=80, n_words=2000, median=2500, lo=50, hi=20000, block_docs=128)
     _autotune_and_check(wl, oracle_index(wl), device_index(wl))
+
+
+def test_slice_width_rules(compact):
+    # 256-byte slices are the one-hash default (128 for the TMA feed and for more
+    # hashes), and only one hash may use them
+    wl, ref, dix = compact
+    for feed, width in ((0, 256), (2, 128)):
+        eng = cobs.Engine(dix, gather_feed=feed)
+        got = eng.query_host(wl.queries, wl.q_off, wl.thresholds, cobs.COBS_GRAPH)
+        assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
+        assert eng.stats()["slice_bytes"] == width
+    wl3 = synth.config4(n_docs=40, n_q=5, n_words=500, median=800, lo=50, hi=2000, block_docs=16)
+    dix3 = device_index(wl3)
+    with pytest.raises(cobs.CobsError) as e:
+        cobs.Engine(dix3, slice_bytes=256)
+    assert e.value.status == cobs.COBS_ERR_ARG
+    eng3 = cobs.Engine(dix3)
+    eng3.query_host(wl3.queries, wl3.q_off, wl3.thresholds, cobs.COBS_BATCHED)
+    assert eng3.stats()["slice_bytes"] == 128

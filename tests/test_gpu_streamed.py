@@ -80,7 +80,7 @@ def test_streamed_errors(streamed):
     assert e.value.status == cobs.COBS_ERR_ARG
 
 
-@pytest.mark.parametrize("slice_bytes", [32, 128])
+@pytest.mark.parametrize("slice_bytes", [32, 128, 256])
 @pytest.mark.parametrize("slots", [1, 2])
 def test_streamed_wide_rows_in_column_units(slice_bytes, slots):
     # blocks of 5,000 and 1,300 documents: rows of 640 and 176 bytes, so the first
