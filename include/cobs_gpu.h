@@ -229,7 +229,8 @@ typedef struct cobs_engine_cfg {
     uint64_t max_query_bytes;
     uint64_t max_hits;        /* initial hit capacity (0 = 1M); grows and re-runs on overflow */
     uint32_t slice_bytes;     /* batched row-slice width: 32, 64, 128, or 256 with one hash;
-                                 0 = default (256 with one hash, else 128; 128 for gather_feed 2) */
+                                 0 = default (256 with one hash when the blocks' rows pad to at most
+                                 2 % more bytes than with 128, else 128; 128 for gather_feed 2) */
     uint32_t ctas_per_sm;     /* persistent grid = SMs * ctas_per_sm; 0 = full occupancy */
     uint32_t l2_hints;        /* L2 eviction priority of the batched gather's loads:
                                  0 = default (4), 1 = none, 2 = row indices evict-first,

@@ -1063,8 +1063,16 @@ extern "C" cobs_status cobs_engine_create(cobs_device_index *dix, const cobs_eng
     cudaDeviceGetAttribute(&eng->n_sm, cudaDevAttrMultiProcessorCount, dev);
     // default slice width: 256 bytes with one hash (its index rows are read once
     // per two 128-byte columns: gather 0.728 ms against 0.742 ms on the bench
-    // batch), 128 bytes with more hashes and for the TMA feed
-    const uint32_t sb_default = dix->params.num_hashes == 1 && eng->cfg.gather_feed != 2 ? 256 : 128;
+    // batch) unless the blocks' rows would leave more lanes idle than with 128
+    // (a 640-byte row is 3 slices of 256: 1.10 ms against 0.95 ms on a view of
+    // two such blocks); 128 bytes with more hashes and for the TMA feed
+    uint64_t pad128 = 0, pad256 = 0;
+    for (const auto &B : dix->blocks) {
+        pad128 += (B.rowbytes + 127) / 128 * 128;
+        pad256 += (B.rowbytes + 255) / 256 * 256;
+    }
+    const bool wide = pad256 * 50 <= pad128 * 51;  // at most 2 % more lane-bytes
+    const uint32_t sb_default = dix->params.num_hashes == 1 && eng->cfg.gather_feed != 2 && wide ? 256 : 128;
     uint32_t sb = eng->cfg.slice_bytes ? eng->cfg.slice_bytes : sb_default;
     if (sb != 32 && sb != 64 && sb != 128 && !(sb == 256 && dix->params.num_hashes == 1)) {
         delete eng;

@@ -379,14 +379,28 @@ def test_autotune_three_hashes():
 
 
 def test_slice_width_rules(compact):
-    # 256-byte slices are the one-hash default (128 for the TMA feed and for more
-    # hashes), and only one hash may use them
+    # 256-byte slices are the one-hash default when the blocks' rows pad to at
+    # most 2 % more bytes than with 128-byte slices (128 otherwise, for the TMA
+    # feed and for more hashes); only one hash may use them
+    def expected(dix):
+        rbs = [b["rowbytes"] for b in dix.info()["blocks"]]
+        p128 = sum(-(-r // 128) * 128 for r in rbs)
+        p256 = sum(-(-r // 256) * 256 for r in rbs)
+        return 256 if p256 * 50 <= p128 * 51 else 128
+
+    lens = np.full(8192, 60, np.uint64)  # one block of 8,192 documents: 1,024-byte rows
+    docs, off = synth.dna_docs(401, lens)
+    qb, qo, src = synth.dna_queries(402, 20, docs, off, n_tp=20, fixed_len=50, rate_lo=0.0, rate_hi=0.0)
+    wide = synth.Workload("wide", 0, 31, 1, 0.3, 8192, 32, docs, off, qb, qo, np.full(20, 1000, np.uint16), src)
     wl, ref, dix = compact
-    for feed, width in ((0, 256), (2, 128)):
-        eng = cobs.Engine(dix, gather_feed=feed)
-        got = eng.query_host(wl.queries, wl.q_off, wl.thresholds, cobs.COBS_GRAPH)
-        assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
-        assert eng.stats()["slice_bytes"] == width
+    cases = [(wl, ref, dix), (wide, oracle_index(wide), device_index(wide))]
+    assert [expected(c[2]) for c in cases] == [128, 256]
+    for w, r, d in cases:
+        for feed in (0, 2):
+            eng = cobs.Engine(d, gather_feed=feed)
+            got = eng.query_host(w.queries, w.q_off, w.thresholds, cobs.COBS_GRAPH)
+            assert_results_equal(got, r, w.query_list(), w.thresholds)
+            assert eng.stats()["slice_bytes"] == (expected(d) if feed == 0 else 128)
     wl3 = synth.config4(n_docs=40, n_q=5, n_words=500, median=800, lo=50, hi=2000, block_docs=16)
     dix3 = device_index(wl3)
     with pytest.raises(cobs.CobsError) as e:
