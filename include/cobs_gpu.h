@@ -260,7 +260,10 @@ void cobs_engine_free(cobs_engine *eng);
  * offsets_host is a host copy of the offsets used to plan tiles (must equal the
  * device array).  Asynchronous: results stay on the device (see
  * cobs_engine_results_device) and are complete when the engine stream reaches
- * this point. */
+ * this point.  A batch still in flight on the engine is waited for first (its
+ * results, if not collected, are dropped).  After a failed call (e.g. OOM) the
+ * engine stays usable; the calls that collect results return ARG until a batch
+ * has been queued in full. */
 cobs_status cobs_engine_query_device(cobs_engine *eng, const uint8_t *queries_dev, const uint64_t *offsets_dev,
                                      const uint64_t *offsets_host, const uint16_t *thr_dev, uint64_t n,
                                      uint32_t flags);
