@@ -107,3 +107,32 @@ def test_product_path_does_not_touch_the_oracle():
             if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 src = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in src and "orc_" not in src and "liboracle" not in src, fn
+
+
+def test_header_is_plain_c(tmp_path):
+    # the boundary header compiles as C99 and as C++ with every warning an error,
+    # and a C program that takes the address of every declared function links
+    # against the library
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    names = sorted(_declared_functions())
+    body = "\n".join(f"    (any_fn)&{n}," for n in names)
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "cobs_gpu.h"\n#include <stdio.h>\ntypedef void (*any_fn)(void);\n'
+                   f"static const any_fn fns[] = {{\n{body}\n}};\n"
+                   'int main(void) { printf("%d\\n", (int)(sizeof fns / sizeof fns[0])); return 0; }\n')
+    inc = os.path.join(ROOT, "include")
+    lib = cobs.lib()._name
+    exe = tmp_path / "use_header"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc, str(src),
+                        lib, "-o", str(exe), f"-Wl,-rpath,{os.path.dirname(lib)}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and int(r.stdout) == len(names), r.stdout + r.stderr
+    cpp = tmp_path / "use_header.cpp"
+    cpp.write_text('#include "cobs_gpu.h"\nint main() { return 0; }\n')
+    r = subprocess.run(["g++", "-std=c++17", "-Wall", "-Wextra", "-Werror", "-I", inc, "-c", str(cpp), "-o",
+                        str(tmp_path / "use_header.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
