@@ -46,8 +46,11 @@ def _digest(paths, extra):
     return h.hexdigest()
 
 
-def build(verbose: bool = False, ptxas_verbose: bool = False, extra_flags=()) -> str:
-    """Build (or reuse) the library; returns its path."""
+def build(verbose: bool = False, ptxas_verbose: bool = False, extra_flags=(), lib_path: str = LIB,
+          link_flags=()) -> str:
+    """Build (or reuse) the library; returns its path.  lib_path / extra_flags /
+    link_flags build a variant elsewhere (the tests build one whose host code
+    runs under AddressSanitizer + UBSan)."""
     nvcc = _nvcc()
     flags = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
              "-I", INCLUDE, "-I", CSRC] + ARCH + list(extra_flags)
@@ -56,12 +59,13 @@ def build(verbose: bool = False, ptxas_verbose: bool = False, extra_flags=()) ->
     if ptxas_verbose:
         flags += ["-Xptxas", "-v"]
     srcs = _sources()
-    stamp_val = _digest(srcs + _headers(), " ".join(flags) + nvcc)
-    stamp = LIB + ".stamp"
-    if os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == stamp_val:
-        return LIB
-    os.makedirs(LIBDIR, exist_ok=True)
-    objs = [os.path.join(LIBDIR, os.path.splitext(os.path.basename(s))[0] + ".o") for s in srcs]
+    stamp_val = _digest(srcs + _headers(), " ".join(flags) + " ".join(link_flags) + nvcc)
+    stamp = lib_path + ".stamp"
+    if os.path.exists(lib_path) and os.path.exists(stamp) and open(stamp).read() == stamp_val:
+        return lib_path
+    libdir = os.path.dirname(lib_path)
+    os.makedirs(libdir, exist_ok=True)
+    objs = [os.path.join(libdir, os.path.splitext(os.path.basename(s))[0] + ".o") for s in srcs]
 
     def compile_one(src_obj):
         src, obj = src_obj
@@ -77,15 +81,15 @@ def build(verbose: bool = False, ptxas_verbose: bool = False, extra_flags=()) ->
         for s, log in zip(srcs, logs):
             if log.strip():
                 print(f"== {os.path.basename(s)}\n{log}")
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lpthread", "-ldl"]
+    tmp = lib_path + f".{os.getpid()}.tmp"
+    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lpthread", "-ldl"] + list(link_flags)
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib_path)
     with open(stamp, "w") as f:
         f.write(stamp_val)
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":

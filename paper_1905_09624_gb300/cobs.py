@@ -144,11 +144,13 @@ SERVE_PROTOS = {k: _PROTOS[k] for k in ("cobs_serve_submit", "cobs_serve_poll", 
 _lib = None
 
 
-def lib(build: bool = True):
-    """Load libcobs_gpu.so (building it first when `build`)."""
+def lib(build: bool = True, path: str | None = None):
+    """Load libcobs_gpu.so (building it first when `build`); `path` loads another
+    build of the library instead (it must be the first call)."""
     global _lib
     if _lib is None:
-        path = _build.build() if build else _build.LIB
+        if path is None:
+            path = _build.build() if build else _build.LIB
         if not os.path.exists(path):
             raise RuntimeError(f"libcobs_gpu.so not found at {path}; run the build first")
         L = ctypes.CDLL(path)
