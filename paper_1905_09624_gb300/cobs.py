@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -234,7 +235,30 @@ def result_to_arrays(res_ptr):
     return h["n_terms"].copy(), h["min_score"].copy(), off, ids, sc
 
 
-class HostIndex:
+class _Owned:
+    """Explicit release: close() (also on leaving a `with` block) frees the
+    object now instead of when it is collected.  A device index refuses while an
+    engine, a server or a multi-index view that uses it is still open."""
+
+    def _depends_on(self, other):
+        users = other.__dict__.setdefault("_users", weakref.WeakSet())
+        users.add(self)
+
+    def close(self):
+        live = [u for u in self.__dict__.get("_users", ()) if getattr(u, "h", None)]
+        if live:
+            raise RuntimeError(f"close the {len(live)} object(s) using this {type(self).__name__} first")
+        self.__del__()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+
+class HostIndex(_Owned):
     """cobs_index (host copy)."""
 
     def __init__(self, handle):
@@ -285,7 +309,7 @@ class HostIndex:
         return HostIndex(h.value)
 
 
-class DeviceIndex:
+class DeviceIndex(_Owned):
     """cobs_device_index (resident in HBM)."""
 
     def __init__(self, handle):
@@ -328,6 +352,8 @@ class DeviceIndex:
         check(lib().cobs_multi_index_create(arr, len(parts), ctypes.byref(h)), "cobs_multi_index_create")
         view = DeviceIndex(h.value)
         view._parts = list(parts)  # the view borrows their rows
+        for p in parts:
+            view._depends_on(p)
         return view
 
     @staticmethod
@@ -365,12 +391,13 @@ class DeviceIndex:
         return result_to_python(res)
 
 
-class Engine:
+class Engine(_Owned):
     """cobs_engine: reusable query workspace on one device index."""
 
     def __init__(self, dix: DeviceIndex, stream=None, slice_bytes=0, ctas_per_sm=0, max_hits=0, l2_hints=0, split=0,
                  stage_bytes=0, gather_feed=0):
         self.dix = dix
+        self._depends_on(dix)
         cfg = cobs_engine_cfg(0, 0, max_hits, slice_bytes, ctas_per_sm, l2_hints, split, stage_bytes, gather_feed, 0)
         h = vp()
         check(lib().cobs_engine_create(dix.h, ctypes.byref(cfg), stream, ctypes.byref(h)), "cobs_engine_create")
@@ -441,12 +468,13 @@ class Engine:
         return dict(slice_bytes=cfg.slice_bytes, ctas_per_sm=cfg.ctas_per_sm, l2_hints=cfg.l2_hints)
 
 
-class Server:
+class Server(_Owned):
     """cobs_server: continuous-batching serve loop."""
 
     def __init__(self, dix: DeviceIndex, score_budget_bytes=0, max_inflight_waves=0, max_wave_queries=0,
                  wait_timeout_ms=0):
         self.dix = dix
+        self._depends_on(dix)
         self._L = lib()
         cfg = cobs_serve_cfg(score_budget_bytes, max_inflight_waves, max_wave_queries, wait_timeout_ms, 0)
         h = vp()

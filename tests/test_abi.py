@@ -136,3 +136,18 @@ def test_header_is_plain_c(tmp_path):
     r = subprocess.run(["g++", "-std=c++17", "-Wall", "-Wextra", "-Werror", "-I", inc, "-c", str(cpp), "-o",
                         str(tmp_path / "use_header.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_host_index_close(tmp_path):
+    # close() and with-blocks release a host index at once (no GPU involved)
+    import oracle as orc
+    import synth
+    lens = synth.lognormal_lengths(3, 10, 300, 0.3, 50, 600)
+    docs, off = synth.dna_docs(3, lens)
+    ix = orc.build_index(orc.make_params(block_docs=4), docs, off)
+    path = str(tmp_path / "x.idx")
+    _write_index_file(path, cobs.make_params(block_docs=4), ix.blocks(), ix.perm(), ix.nterms(), ix.rows())
+    with cobs.HostIndex.load(path) as h:
+        assert h.info()["n_docs"] == 10
+    assert h.h is None
+    h.close()  # closing twice is harmless

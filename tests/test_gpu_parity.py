@@ -409,3 +409,25 @@ def test_slice_width_rules(compact):
     eng3 = cobs.Engine(dix3)
     eng3.query_host(wl3.queries, wl3.q_off, wl3.thresholds, cobs.COBS_BATCHED)
     assert eng3.stats()["slice_bytes"] == 128
+
+
+def test_explicit_release_order(compact):
+    # close() / with-blocks free objects at once; a device index refuses to close
+    # while an engine, a server or a multi-index view on it is open
+    wl, ref, _ = compact
+    dix = device_index(wl)
+    with cobs.Engine(dix) as eng:
+        got = eng.query_host(wl.queries, wl.q_off, wl.thresholds, cobs.COBS_BATCHED)
+        assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
+        with pytest.raises(RuntimeError):
+            dix.close()
+    srv = cobs.Server(dix)
+    view = cobs.DeviceIndex.multi([dix])
+    with pytest.raises(RuntimeError):
+        dix.close()
+    srv.close()
+    with pytest.raises(RuntimeError):
+        dix.close()
+    view.close()
+    dix.close()
+    assert dix.h is None
