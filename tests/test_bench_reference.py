@@ -26,3 +26,16 @@ def test_bench_rejects_short_warmup():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--warmup", "2"], capture_output=True,
                        text=True, timeout=120, cwd=ROOT)
     assert r.returncode != 0 and "warmup" in r.stderr
+
+
+def test_traffic_record_matches_the_gather_sources():
+    # the committed ncu record (roofline.traffic) was taken on the gather
+    # kernel as it is now: its source hash matches, and it states the slice width
+    # and the physical DRAM bytes of one launch
+    sys.path.insert(0, ROOT)
+    import bench
+    csrc = os.path.join(ROOT, "paper_1905_09624_gb300", "csrc")
+    rec = bench.traffic_record([os.path.join(csrc, "gather.cu"), os.path.join(csrc, "gather_common.cuh")])
+    assert rec is not None, "gather sources changed since profiles/gather_batched_cfg2_dram.txt was captured"
+    assert rec["slice_bytes"] in (128, 256)
+    assert 0.6e9 < rec["dram_bytes"] < 12.26e9  # at least the index once, at most the logical row bytes
