@@ -365,3 +365,36 @@ def test_false_positive_statistics_binomial():
     assert chi2d.sf(chi2, dof) > 1e-4, (chi2, dof)
     # mean score matches l * mean fill
     assert pooled @ np.arange(71) / (24 * n70) == pytest.approx(70 * fill.mean(), rel=0.02)
+
+
+def test_generated_inputs_exact_mode_and_superset():
+    # Generated small corpora (ACGT with some N, empty and short documents, k = 1..6,
+    # 1-2 hashes, classic and tiny blocks): in exact mode (identity hash, w = 4^k)
+    # every score equals brute-force containment; with XXH64 every score is at
+    # least the containment (Sec. 2.2: one-sided error).
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=60, deadline=None, derandomize=True)
+    @hyp.given(docs=st.lists(st.text(alphabet="ACGTN", max_size=60), min_size=1, max_size=7),
+               query=st.text(alphabet="ACGTN", max_size=40), k=st.integers(1, 6), h=st.integers(1, 2),
+               block_docs=st.sampled_from([0, 1, 2, 3]), canonical=st.booleans())
+    def check(docs, query, k, h, block_docs, canonical):
+        raw = [d.encode() for d in docs]
+        buf = np.frombuffer(b"".join(raw) or b"\0", dtype=np.uint8)[:sum(len(r) for r in raw)].copy()
+        off = np.zeros(len(raw) + 1, np.uint64)
+        off[1:] = np.cumsum([len(r) for r in raw])
+        kind = 0 if canonical else 1
+        q = query.encode()
+        bl, bs = _brute_scores(buf, off, q, k, kind)
+        exact = oracle.build_index(oracle.make_params(term_kind=kind, q=k, num_hashes=h, fpr=0.3,
+                                                      block_docs=block_docs, hash_kind=oracle.HASH_IDENTITY,
+                                                      width_override=4 ** k), buf, off)
+        l, sc = exact.scores(q)
+        assert (l, list(sc)) == (bl, bs)
+        bloom = oracle.build_index(oracle.make_params(term_kind=kind, q=k, num_hashes=h, fpr=0.3,
+                                                      block_docs=block_docs), buf, off)
+        l2, sc2 = bloom.scores(q)
+        assert l2 == bl and all(a >= b for a, b in zip(sc2.tolist(), bs))
+
+    check()
