@@ -182,7 +182,10 @@ def test_cancel_queued_and_in_flight(mock_lib):
     # one slot; wave 0 hangs until released, so later tickets wait in the queue
     srv = start(mock_lib, slots=1, hang=0, wave_max=1)
     t0 = srv.submit(b"ACGTACGT", 500)
-    time.sleep(0.02)  # wave 0 is launched
+    deadline = time.time() + 10
+    while stats(mock_lib).launched_waves < 1:  # wave 0 (t0) is on the device
+        assert time.time() < deadline
+        time.sleep(0.001)
     queued = [srv.submit(b"ACGTAC" + bytes([65 + i]), 500) for i in range(5)]
     srv.cancel(t0)         # on the device: result dropped when its wave ends
     srv.cancel(queued[1])  # in the queue: never launched
@@ -231,6 +234,10 @@ def test_timeout_and_slot_recovery(mock_lib):
     srv = start(mock_lib, slots=2, hang=0, wave_max=1, timeout_ms=100)
     t0 = srv.submit(b"ACGTACGT", 500)
     t_start = time.time()
+    deadline = t_start + 10
+    while stats(mock_lib).launched_waves < 1:  # wave 0 (t0) hangs on the first slot
+        assert time.time() < deadline
+        time.sleep(0.001)
     others = [srv.submit(b"ACGTACG" + bytes([65 + i % 4]), 500) for i in range(10)]
     for t in others:
         assert wait(srv, t)[0] == 5
