@@ -400,6 +400,12 @@ uint64_t cobs_bloom_width(uint32_t h, uint64_t v, double p);
 /* Library version string. */
 const char *cobs_version(void);
 
+/* Version of this header's types and entry points; it changes whenever a struct
+ * layout or a signature changes.  A caller built against this header checks
+ * cobs_abi_version() == COBS_GPU_ABI_VERSION before using the library. */
+#define COBS_GPU_ABI_VERSION 3u
+uint32_t cobs_abi_version(void);
+
 /* Host-side fault injection for tests (the paper has no counterpart).  After
  * `after` more successful device or pinned-host allocations by the library, every
  * allocation fails as if memory were exhausted, until this is called with a

@@ -26,6 +26,8 @@ COBS_ERR_OVERFLOW = -7
 COBS_ERR_NOT_FOUND = -8
 COBS_ERR_CANCELLED = -9
 
+ABI_VERSION = 3  # COBS_GPU_ABI_VERSION of include/cobs_gpu.h that the structs below mirror
+
 COBS_PLAIN = 1
 COBS_BATCHED = 2
 COBS_GRAPH = 4
@@ -134,6 +136,7 @@ _PROTOS = {
     "cobs_last_error": (ctypes.c_char_p, []),
     "cobs_bloom_width": (ctypes.c_uint64, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double]),
     "cobs_version": (ctypes.c_char_p, []),
+    "cobs_abi_version": (ctypes.c_uint32, []),
     "cobs_debug_fail_alloc": (None, [ctypes.c_int64]),
     "cobs_debug_build_scratch": (None, [ctypes.c_uint64]),
 }
@@ -159,6 +162,9 @@ def lib(build: bool = True, path: str | None = None):
             f = getattr(L, name)
             f.restype = res
             f.argtypes = args
+        if L.cobs_abi_version() != ABI_VERSION:  # the structs above mirror one version of the header
+            raise RuntimeError(f"{path} has ABI version {L.cobs_abi_version()}, this binding expects "
+                               f"{ABI_VERSION}: rebuild the library")
         _lib = L
     return _lib
 

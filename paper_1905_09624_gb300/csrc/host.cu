@@ -32,6 +32,7 @@ using namespace cobs;
     } while (0)
 
 extern "C" const char *cobs_version(void) { return "cobs_gpu 0.1 (sm_103a)"; }
+extern "C" uint32_t cobs_abi_version(void) { return COBS_GPU_ABI_VERSION; }
 
 // --------------------------------------------------------------- planning
 

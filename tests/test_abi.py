@@ -151,3 +151,9 @@ def test_host_index_close(tmp_path):
         assert h.info()["n_docs"] == 10
     assert h.h is None
     h.close()  # closing twice is harmless
+
+
+def test_abi_version_matches_header_and_binding():
+    src = open(os.path.join(ROOT, "include", "cobs_gpu.h")).read()
+    m = re.search(r"#define COBS_GPU_ABI_VERSION (\d+)u", src)
+    assert m and int(m.group(1)) == cobs.ABI_VERSION == cobs.lib().cobs_abi_version()
