@@ -12,8 +12,6 @@ import oracle
 import synth
 from paper_1905_09624_gb300 import cobs
 
-from parity import assert_results_equal
-
 pytestmark = pytest.mark.gpu
 
 P = dict(term_kind=0, q=31, num_hashes=1, fpr=0.3, block_docs=64, score_bits=32)

@@ -4,7 +4,6 @@ units of all ranks by the slowest rank's time."""
 import os
 import socket
 
-import pytest
 import torch.multiprocessing as mp
 
 

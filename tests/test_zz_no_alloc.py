@@ -8,7 +8,6 @@ call it through the C ABI and check its hits against the library's existing
 batched entry point, bit for bit, on consecutive calls that reuse the scratch.
 The file is named so that pytest collects it last.
 """
-import ctypes
 
 import numpy as np
 import pytest
