@@ -17,7 +17,8 @@ Parity status of each function (what pins it, besides itself):
                  inverted index and scores equal brute-force containment.
   query          exact mode as above; no false negatives with XXH64; classic equals
                  compact with one block; false-positive score statistics against the
-                 binomial law of Theorem 1.
+                 binomial law of Theorem 1; generated corpora (exact mode equals
+                 brute-force containment, XXH64 scores never below it).
   binom_tail_ge  the paper's worked example (l=70, p=0.3, K=0.5 -> 0.000143) and
                  exact rational sums on small cases; Chernoff bound >= tail.
 """
