@@ -363,7 +363,7 @@ cobs_status cobs_serve_stop(cobs_server *srv, cobs_serve_stats *out);
  * cobs_query_one_noalloc runs ONE query through the plain kernels (terms,
  * gather/AND/ADD, threshold, sorted hits) and allocates nothing: no cudaMalloc,
  * no cudaFree, no allocating library routine.  Its scratch is a fixed array in
- * the library's device code, about 6.4 MiB, which every GPU that loads the
+ * the library's device code, about 7.1 MiB, which every GPU that loads the
  * library holds until the process exits.  Limits: at most
  * COBS_NOALLOC_MAX_WINDOWS windows in the query, COBS_NOALLOC_MAX_DOCS documents
  * in the index and COBS_NOALLOC_MAX_ROW_LISTS (blocks x hashes); beyond them the
@@ -388,6 +388,26 @@ cobs_status cobs_serve_stop(cobs_server *srv, cobs_serve_stats *out);
 cobs_status cobs_query_one_noalloc(cobs_device_index *dix, const uint8_t *query_dev, uint64_t len,
                                    uint16_t thr_permille, uint32_t *out_meta_dev, uint32_t *out_ids_dev,
                                    uint32_t *out_scores_dev, uint64_t out_capacity, void *stream);
+
+/* -------------------------------------------------------- measurement */
+
+/* L2 read-bandwidth probe (the paper has no counterpart; it measures the ceiling
+ * of a gather whose rows are reused through the L2 cache).  Reads the device
+ * buffer buf_dev of `bytes` bytes (16-byte aligned; sized well inside the L2)
+ * `reps` times with 16-byte loads that bypass L1, from (SMs x ctas_per_sm) CTAs
+ * of 256 threads (ctas_per_sm 0 = 8), queued on `stream`.  The caller times it
+ * with CUDA events: bandwidth = reps x bytes / time.  sink_dev: one device
+ * uint64 the kernel may add to (its value means nothing).  Errors: ARG, CUDA. */
+cobs_status cobs_probe_l2_read(const void *buf_dev, uint64_t bytes, uint32_t reps, uint32_t ctas_per_sm,
+                               void *sink_dev, void *stream);
+
+/* Test hook (the paper has no counterpart): out_dev[i] = x_dev[i] mod w for
+ * i < n, computed by the device's Barrett reduction with the constant an index
+ * uses for a block of Bloom size w -- the reduction behind every row index
+ * (Sec. 2.2: one wide hash, then modulo each filter size).  x_dev (uint64) and
+ * out_dev (uint32) are device arrays; w in 1..2^32 - 1; queued on `stream`.
+ * Errors: ARG (w out of range, NULL arrays), CUDA. */
+cobs_status cobs_debug_barrett_mod(const uint64_t *x_dev, uint64_t n, uint64_t w, uint32_t *out_dev, void *stream);
 
 /* --------------------------------------------------------------- misc */
 

@@ -133,6 +133,8 @@ _PROTOS = {
     "cobs_serve_stop": (ctypes.c_int, [vp, ctypes.POINTER(cobs_serve_stats)]),
     "cobs_query_one_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_uint64, ctypes.c_uint16, vp, vp, vp,
                                               ctypes.c_uint64, vp]),
+    "cobs_probe_l2_read": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, vp, vp]),
+    "cobs_debug_barrett_mod": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint64, vp, vp]),
     "cobs_last_error": (ctypes.c_char_p, []),
     "cobs_bloom_width": (ctypes.c_uint64, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double]),
     "cobs_version": (ctypes.c_char_p, []),
@@ -540,3 +542,15 @@ class Server(_Owned):
 
 def bloom_width(h, v, p):
     return int(lib().cobs_bloom_width(h, v, p))
+
+
+def probe_l2_read(buf_ptr, nbytes, reps, sink_ptr, ctas_per_sm=0, stream=None):
+    """cobs_probe_l2_read on a device buffer (pointers as integers); queued on `stream`."""
+    check(lib().cobs_probe_l2_read(ctypes.c_void_p(buf_ptr), nbytes, reps, ctas_per_sm, ctypes.c_void_p(sink_ptr),
+                                   ctypes.c_void_p(stream)), "cobs_probe_l2_read")
+
+
+def debug_barrett_mod(x_ptr, n, w, out_ptr, stream=None):
+    """cobs_debug_barrett_mod: out[i] = x[i] mod w on the device (pointers as integers)."""
+    check(lib().cobs_debug_barrett_mod(ctypes.c_void_p(x_ptr), n, w, ctypes.c_void_p(out_ptr),
+                                       ctypes.c_void_p(stream)), "cobs_debug_barrett_mod")

@@ -150,6 +150,20 @@ __device__ __forceinline__ bool set_insert(unsigned long long *table, uint32_t c
     return false;  // unreachable for a correctly sized table
 }
 
+// The slot that holds `key` after inserting it (now or by an earlier call), with
+// the probe sequence of set_insert.
+__device__ __forceinline__ uint32_t set_find_insert(unsigned long long *table, uint32_t cap, uint64_t h,
+                                                    uint64_t key) {
+    uint32_t slot = (uint32_t)(((h >> 32) * (uint64_t)cap) >> 32);
+    for (uint32_t probe = 0; probe < cap; probe++) {
+        const unsigned long long old =
+            atomicCAS(&table[slot], (unsigned long long)EMPTY_KEY, (unsigned long long)key);
+        if (old == EMPTY_KEY || old == key) return slot;
+        slot = slot + 1u == cap ? 0u : slot + 1u;
+    }
+    return 0u;  // unreachable for a correctly sized table
+}
+
 // Slots of the distinct-term set for `npos` windows.
 __host__ __device__ __forceinline__ uint64_t set_slots(uint64_t npos) { return npos * 2 < 16 ? 16 : npos * 2; }
 

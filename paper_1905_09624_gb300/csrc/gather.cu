@@ -27,8 +27,7 @@ __device__ __forceinline__ void tile_body(const GatherArgs &a, const DevBlock &b
     const uint32_t *ridx = a.rows_idx + (uint64_t)(block_idx * a.h) * a.tcap + a.term_base[q];
     const uint8_t *colbase = a.rows + blk.row_offset + col;
     accumulate<L, G>(lv, colbase, blk.rowbytes, ridx, a.tcap, a.h, 0u, n);
-    if (n == 0u) return;
-    emit_hits<L>(a, blk, col, q, ell, lv);
+    emit_hits<L, LPQ>(a, blk, col, q, ell, lv, n != 0u);  // every lane of the warp
 }
 
 // Persistent batched kernel.  Tiles are (row slice, group of QPW queries), slice
@@ -192,11 +191,8 @@ __global__ void __launch_bounds__(PIPE_THREADS) k_gather_pipe(GatherArgs a) {
         }
         carry.flush(lv);
         cp_async_wait<0>();
-        if (it.w == ITEM_WHOLE) {
-            if (n) emit_hits<L>(a, blk, col, q, ell, lv);
-        } else if (active) {
-            write_partials<L>(a, blk, col, it.w, lv);  // every part writes, zeros included
-        }
+        emit_hits<L, LPQ>(a, blk, col, q, ell, lv, it.w == ITEM_WHOLE && n != 0u);  // every lane of the warp
+        if (it.w != ITEM_WHOLE && active) write_partials<L>(a, blk, col, it.w, lv);  // every part writes, zeros included
     }
 }
 

@@ -127,42 +127,90 @@ __device__ __forceinline__ void accumulate(uint32_t (&lv)[4][L], const uint8_t *
     }
 }
 
-// Threshold (Sec. 2.1: score >= ceil(K l)) and hit emission of one lane's 128
-// documents after all terms of its query were added.
+// Warp-collective reservation of hit slots: every lane of the warp calls it
+// with its number of hits nh (0 if it emits none).  Lanes of one query are the
+// SEG consecutive lanes of a segment.  One atomic on the global hit counter per
+// warp, one on the query's count per segment with hits; returns the lane's
+// first slot (an exclusive prefix sum over the warp).
+template <int SEG>
+__device__ __forceinline__ unsigned long long reserve_hits(unsigned long long *hit_count, uint32_t *qcount,
+                                                           uint32_t q, uint32_t nh) {
+    static_assert(SEG >= 1 && SEG <= 32 && (SEG & (SEG - 1)) == 0, "segments of a power of two lanes");
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t incl = nh;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, incl, d);
+        if ((int)lane >= d) incl += y;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    if (total == 0u) return 0ULL;
+    unsigned long long base = 0;
+    if (lane == 31u) base = atomicAdd(hit_count, (unsigned long long)total);
+    base = __shfl_sync(FULL, base, 31);
+    uint32_t seg = nh;
+#pragma unroll
+    for (int d = 1; d < SEG; d <<= 1) seg += __shfl_xor_sync(FULL, seg, d);
+    if ((lane & (SEG - 1)) == 0u && seg) atomicAdd(&qcount[q], seg);
+    return base + (incl - nh);
+}
+
+// Threshold masks (Sec. 2.1: score >= ceil(K l)) of one lane's 128 documents
+// (four words of 32) from its vertical counters; documents past the block's end
+// are cleared.  Returns the number of hits.
 template <int L>
-__device__ __forceinline__ void emit_hits(const GatherArgs &a, const DevBlock &blk, uint32_t col, uint32_t q,
-                                          uint32_t ell, const uint32_t (&lv)[4][L]) {
-    const uint32_t mn = (uint32_t)(((uint64_t)a.thr[q] * ell + 999u) / 1000u);
-    const uint32_t doc0 = col * 8u;
-    uint32_t ge[4];
+__device__ __forceinline__ uint32_t threshold_masks(const uint32_t (&lv)[4][L], uint32_t mn, uint32_t doc0,
+                                                    uint32_t n_docs, uint32_t (&ge)[4]) {
     uint32_t nh = 0;
 #pragma unroll
     for (int w = 0; w < 4; w++) {
         uint32_t m = ge_mask<L>(lv[w], mn);
-        uint32_t jw = doc0 + 32u * w;
-        if (jw >= blk.n_docs) m = 0u;
-        else if (blk.n_docs - jw < 32u) m &= (1u << (blk.n_docs - jw)) - 1u;
+        const uint32_t jw = doc0 + 32u * w;
+        if (jw >= n_docs) m = 0u;
+        else if (n_docs - jw < 32u) m &= (1u << (n_docs - jw)) - 1u;
         ge[w] = m;
         nh += __popc(m);
     }
-    if (nh == 0u) return;
-    unsigned long long pos = atomicAdd(a.hit_count, (unsigned long long)nh);
-    atomicAdd(&a.qcount[q], nh);
+    return nh;
+}
+
+// Write a lane's hits from slot pos on: (query, key = (~score << 32) | original id).
+template <int L>
+__device__ __forceinline__ void write_hits(const uint32_t (&lv)[4][L], const uint32_t (&ge)[4], uint32_t q,
+                                           const uint32_t *perm_of_doc0, unsigned long long pos, uint32_t *raw_q,
+                                           unsigned long long *raw_key, uint64_t hit_cap) {
 #pragma unroll
     for (int w = 0; w < 4; w++) {
         uint32_t m = ge[w];
         while (m) {
-            uint32_t bit = __ffs(m) - 1u;
+            const uint32_t bit = __ffs(m) - 1u;
             m &= m - 1u;
-            uint32_t score = count_of<L>(lv[w], bit);
-            uint32_t id = a.perm[blk.doc_begin + doc0 + 32u * w + bit];
-            if (pos < a.hit_cap) {
-                a.raw_q[pos] = q;
-                a.raw_key[pos] = ((unsigned long long)(~score) << 32) | id;
+            const uint32_t score = count_of<L>(lv[w], bit);
+            const uint32_t id = perm_of_doc0[32u * w + bit];
+            if (pos < hit_cap) {
+                raw_q[pos] = q;
+                raw_key[pos] = ((unsigned long long)(~score) << 32) | id;
             }
             pos++;
         }
     }
+}
+
+// Threshold and hit emission of one lane's 128 documents after all terms of its
+// query were added (emit false: the lane has nothing to report).  Warp-collective:
+// every lane of the warp calls it; the lanes of one query are SEG consecutive lanes.
+template <int L, int SEG>
+__device__ __forceinline__ void emit_hits(const GatherArgs &a, const DevBlock &blk, uint32_t col, uint32_t q,
+                                          uint32_t ell, const uint32_t (&lv)[4][L], bool emit) {
+    uint32_t ge[4] = {0u, 0u, 0u, 0u};
+    uint32_t nh = 0;
+    const uint32_t doc0 = col * 8u;
+    if (emit) {
+        const uint32_t mn = (uint32_t)(((uint64_t)a.thr[q] * ell + 999u) / 1000u);
+        nh = threshold_masks<L>(lv, mn, doc0, blk.n_docs, ge);
+    }
+    const unsigned long long pos = reserve_hits<SEG>(a.hit_count, a.qcount, q, nh);
+    if (nh) write_hits<L>(lv, ge, q, a.perm + blk.doc_begin + doc0, pos, a.raw_q, a.raw_key, a.hit_cap);
 }
 
 // A split item's counts for the lane's 128 documents (each below 2^16).

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(PH_THREADS) k_gather_pipe_h(GatherArgs a) {
         }
         carry.flush(lv);
         cp_async_wait<0>();
-        if (n) emit_hits<L>(a, blk, col, q, ell, lv);
+        emit_hits<L, LPQ>(a, blk, col, q, ell, lv, n != 0u);  // every lane of the warp
     }
 }
 

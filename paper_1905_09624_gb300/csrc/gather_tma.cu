@@ -154,11 +154,8 @@ __global__ void __launch_bounds__(TG_THREADS) k_gather_tma(GatherArgs a) {
         }
         carry.flush(lv);
         const uint32_t n = active ? nq : 0u;
-        if (it.w == ITEM_WHOLE) {
-            if (n) emit_hits<L>(a, blk, col, q, ell, lv);
-        } else if (active) {
-            write_partials<L>(a, blk, col, it.w, lv);  // every part writes, zeros included
-        }
+        emit_hits<L, 8>(a, blk, col, q, ell, lv, it.w == ITEM_WHOLE && n != 0u);  // every lane of the warp
+        if (it.w != ITEM_WHOLE && active) write_partials<L>(a, blk, col, it.w, lv);  // every part writes, zeros included
     }
 }
 

@@ -85,17 +85,17 @@ static cobs_status plan_index(const cobs_params &P, const std::vector<uint64_t> 
     return COBS_OK;
 }
 
-static uint64_t barrett_m_of(uint64_t w) {
+uint64_t cobs::barrett_m_of(uint64_t w) {
     if (w <= 1) return ~0ULL;
     unsigned __int128 one = (unsigned __int128)1 << 64;
     return (uint64_t)(one / w);
 }
 
-// Upload the block table, permutation and column maps of a device index.
+// Upload the block table, permutation and column groups of a device index.
 static cobs_status upload_tables(cobs_device_index *dix, cudaStream_t s) {
     const uint64_t nb = dix->blocks.size();
     std::vector<DevBlock> db(nb);
-    std::vector<uint32_t> cb, cy;
+    std::vector<SliceDesc> pg;
     for (uint64_t b = 0; b < nb; b++) {
         const cobs_block_info &B = dix->blocks[b];
         db[b].row_offset = dix->dev_row_offset.empty() ? B.row_offset : dix->dev_row_offset[b];
@@ -104,24 +104,18 @@ static cobs_status upload_tables(cobs_device_index *dix, cudaStream_t s) {
         db[b].rowbytes = (uint32_t)B.rowbytes;
         db[b].n_docs = (uint32_t)B.n_docs;
         db[b].doc_begin = (uint32_t)B.doc_begin;
-        for (uint64_t c = 0; c < B.rowbytes / 16; c++) {
-            cb.push_back((uint32_t)b);
-            cy.push_back((uint32_t)(c * 16));
-        }
+        for (uint64_t c = 0; c < B.rowbytes; c += PLAIN_GROUP_BYTES) pg.push_back(SliceDesc{(uint32_t)b, (uint32_t)c});
     }
-    dix->n_cols = (uint32_t)cb.size();
+    dix->n_pgroups = (uint32_t)pg.size();
     std::vector<uint32_t> p32(dix->n_docs);
     for (uint64_t i = 0; i < dix->n_docs; i++) p32[i] = (uint32_t)dix->perm[i];
     CU(dix->dblocks.ensure(nb * sizeof(DevBlock)));
     CU(dix->dperm.ensure(dix->n_docs * 4));
-    CU(dix->col_block.ensure(cb.size() * 4));
-    CU(dix->col_byte.ensure(cy.size() * 4));
+    CU(dix->pgroups.ensure(pg.size() * sizeof(SliceDesc)));
     if (nb) CU(cudaMemcpyAsync(dix->dblocks.p, db.data(), nb * sizeof(DevBlock), cudaMemcpyHostToDevice, s));
     if (dix->n_docs) CU(cudaMemcpyAsync(dix->dperm.p, p32.data(), dix->n_docs * 4, cudaMemcpyHostToDevice, s));
-    if (!cb.empty()) {
-        CU(cudaMemcpyAsync(dix->col_block.p, cb.data(), cb.size() * 4, cudaMemcpyHostToDevice, s));
-        CU(cudaMemcpyAsync(dix->col_byte.p, cy.data(), cy.size() * 4, cudaMemcpyHostToDevice, s));
-    }
+    if (!pg.empty())
+        CU(cudaMemcpyAsync(dix->pgroups.p, pg.data(), pg.size() * sizeof(SliceDesc), cudaMemcpyHostToDevice, s));
     CU(cudaStreamSynchronize(s));
     return COBS_OK;
 }
@@ -1224,6 +1218,14 @@ static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n
         bp.max_npos = std::max(bp.max_npos, np);
     }
     if (bp.tcap == 0) bp.tcap = TERM_ALIGN;
+    bp.plain_max_chunks = 1;
+    if (!batched) {
+        for (uint64_t q = 0; q < n; q++) {
+            uint32_t ct = 0;
+            bp.plain_max_chunks = std::max(bp.plain_max_chunks, plain_chunks(bp.npos[q], eng->dix->n_pgroups,
+                                                                             (uint32_t)eng->n_sm, PLAIN_MAX_CHUNKS, &ct));
+        }
+    }
     bp.long_q.clear();
     bp.chunk_q.clear();
     bp.chunk_w0.clear();
@@ -1359,7 +1361,8 @@ static cobs_status ensure_buffers(cobs_engine *eng, const BatchPlan &bp) {
     CU(eng->tmp.ensure(eng->hit_cap * 8));
     CU(eng->out_ids.ensure(eng->hit_cap * 4));
     CU(eng->out_scores.ensure(eng->hit_cap * 4));
-    CU(eng->scores.ensure(eng->dix->n_docs * 4));
+    CU(eng->plain_part.ensure(plain_partial_words(eng->dix->n_pgroups, bp.plain_max_chunks) * 4));
+    CU(eng->tickets.ensure((uint64_t)eng->dix->n_pgroups * 4));
     CU(eng->pin_plan.ensure(plan_bytes(bp) + 64));
     CU(eng->pin_count.ensure(16 * 8));
     return COBS_OK;
@@ -1424,42 +1427,74 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
     ta.smem_slots = bp.smem_slots;
 
     if (flags & COBS_PLAIN) {
-        // One query per kernel sequence: terms, zero scores, gather, threshold.
+        // One query per launch over (column group x term chunk) tiles, which
+        // threshold and emit the query's hits themselves (the tickets start at
+        // zero and every query's last tiles leave them at zero).  A query of at
+        // most one term round: the fused kernel alone, a programmatic dependent
+        // of the previous query's, so the two overlap until the epilogue.  A
+        // longer one: its terms kernels (a CTA per round of windows for a long
+        // query), then the gather kernel.
         if (timed) CU(cudaEventRecordWithFlags(eng->ev[1], s, tflag));
+        if (dix->n_pgroups) CU(cudaMemsetAsync(eng->tickets.p, 0, (uint64_t)dix->n_pgroups * 4, s));
+        PlainArgs pa{};
+        pa.rows = dix->dev_rows();
+        pa.blocks = dix->dblocks.as<DevBlock>();
+        pa.groups = dix->pgroups.as<SliceDesc>();
+        pa.n_groups = dix->n_pgroups;
+        pa.h = P.num_hashes;
+        pa.perm = dix->dperm.as<uint32_t>();
+        pa.rows_idx = eng->rows_idx.as<uint32_t>();
+        pa.tcap = bp.tcap;
+        pa.term_base = term_base;
+        pa.ell = eng->ell.as<uint32_t>();
+        pa.thr = d_thr;
+        pa.partials = eng->plain_part.as<uint32_t>();
+        pa.tickets = eng->tickets.as<uint32_t>();
+        pa.hit_count = ctr;
+        pa.qcount = eng->qcount.as<uint32_t>();
+        pa.raw_q = eng->raw_q.as<uint32_t>();
+        pa.raw_key = eng->raw_key.as<unsigned long long>();
+        pa.hit_cap = eng->hit_cap;
+        pa.bytes = d_bytes;
+        pa.offsets = d_off;
+        pa.kind = P.term_kind;
+        pa.k = P.q;
+        const uint64_t round = terms_round_windows();
+        uint32_t li = 0, ci = 0;  // the next long query and its first chunk in the batch plan
         for (uint64_t q = 0; q < n; q++) {
-            ta.q0 = (uint32_t)q;
-            launch_query_terms(ta, 1, s);
-            CU(cudaMemsetAsync(eng->scores.p, 0, dix->n_docs * 4, s));
-            PlainArgs pa{};
-            pa.rows = dix->dev_rows();
-            pa.blocks = dix->dblocks.as<DevBlock>();
-            pa.col_block = dix->col_block.as<uint32_t>();
-            pa.col_byte = dix->col_byte.as<uint32_t>();
-            pa.n_cols = dix->n_cols;
-            pa.rows_idx = eng->rows_idx.as<uint32_t>();
-            pa.tcap = bp.tcap;
-            pa.term_base = term_base;
-            pa.ell = eng->ell.as<uint32_t>();
-            pa.h = P.num_hashes;
+            const uint64_t np = bp.npos[q];
             pa.q = (uint32_t)q;
-            pa.scores = eng->scores.as<uint32_t>();
-            uint32_t chunks = (uint32_t)((bp.npos[q] + PLAIN_CHUNK - 1) / PLAIN_CHUNK);
-            launch_gather_plain(pa, chunks, s);
-            ThresholdArgs th{};
-            th.scores = eng->scores.as<uint32_t>();
-            th.perm = dix->dperm.as<uint32_t>();
-            th.n_docs = (uint32_t)dix->n_docs;
-            th.ell = eng->ell.as<uint32_t>();
-            th.thr = d_thr;
-            th.q = (uint32_t)q;
-            th.hit_count = ctr;
-            th.qcount = eng->qcount.as<uint32_t>();
-            th.raw_q = eng->raw_q.as<uint32_t>();
-            th.raw_key = eng->raw_key.as<unsigned long long>();
-            th.hit_cap = eng->hit_cap;
-            launch_plain_threshold(th, s);
-            eng->stat_launches += 3 + (chunks ? 1 : 0);
-            eng->stat_gather_launches += chunks ? 1 : 0;
+            pa.n_chunks = plain_chunks(np, dix->n_pgroups, (uint32_t)eng->n_sm, PLAIN_MAX_CHUNKS, &pa.chunk_terms);
+            if (plain_fused_fits(np, P.num_hashes)) {
+                CU(launch_plain_fused(pa, (uint32_t)np, true, s));
+                eng->stat_launches += 1;
+            } else {
+                ta.q0 = (uint32_t)q;
+                if (np > round) {
+                    const uint32_t nch = (uint32_t)((np + round - 1) / round);
+                    CU(cudaMemsetAsync(eng->tables.as<unsigned long long>() + bp.table_base[q], 0xFF,
+                                       set_slots(np) * 8, s));
+                    CU(cudaMemsetAsync(eng->ell.as<uint32_t>() + q, 0, 4, s));
+                    CU(cudaMemsetAsync(eng->long_flag.as<uint32_t>() + q, 0, 4, s));
+                    TermsArgs tl = ta;
+                    tl.long_q = long_q + li;
+                    tl.chunk_q = chunk_q + ci;
+                    tl.chunk_w0 = chunk_w0 + ci;
+                    tl.long_flag = eng->long_flag.as<uint32_t>();
+                    tl.n_long = 1;
+                    tl.n_chunks = nch;
+                    launch_query_terms(tl, 1, s);
+                    li += 1;
+                    ci += nch;
+                    eng->stat_launches += 3;
+                } else {
+                    launch_query_terms(ta, 1, s);
+                    eng->stat_launches += 1;
+                }
+                CU(launch_plain_query(pa, counter_levels_for((uint32_t)np), s));
+                eng->stat_launches += 1;
+            }
+            eng->stat_gather_launches += 1;
         }
         CU(cudaGetLastError());
         if (timed) CU(cudaEventRecordWithFlags(eng->ev[2], s, tflag));

@@ -93,6 +93,7 @@ struct BatchPlan {
     std::vector<Item> split;        // split queries: (query, first slot, slots, 0)
     uint64_t n_parts = 0;           // partial slots
     uint32_t part_terms = 0;        // terms per part of the split queries
+    uint32_t plain_max_chunks = 1;  // plain form: most term chunks of a query of the batch
     // long queries (more windows than one round of the term kernel): one term
     // CTA per round (chunk), then one row CTA per (query, block group)
     std::vector<uint32_t> long_q, chunk_q, chunk_w0;
@@ -101,6 +102,10 @@ struct BatchPlan {
 };
 
 struct ResultStore;
+
+// Barrett constant floor(2^64 / w) of a Bloom size w (UINT64_MAX for w <= 1),
+// the per-block modulus constant of barrett_mod.
+uint64_t barrett_m_of(uint64_t w);
 
 }  // namespace cobs
 
@@ -119,8 +124,8 @@ struct cobs_device_index {
     std::vector<cobs_block_info> blocks;
     std::vector<uint64_t> perm, nterms;
     uint64_t rows_bytes = 0;
-    uint32_t n_cols = 0;  // 16-byte columns over all blocks (plain kernel)
-    cobs::DevBuf rows, dblocks, dperm, col_block, col_byte;
+    uint32_t n_pgroups = 0;  // 128-byte column groups over all blocks (plain kernel)
+    cobs::DevBuf rows, dblocks, dperm, pgroups;
     // streamed index: rows in pinned host memory, copied block by block per batch
     bool streamed = false;
     cobs::PinBuf host_rows;
@@ -155,7 +160,8 @@ struct cobs_engine {
     cobs::DevBuf counters;                    // [0] hit count, [1..] work counters
     cobs::DevBuf rows_idx, tables, codes;
     cobs::DevBuf raw_q, raw_key, keys, tmp, out_ids, out_scores;
-    cobs::DevBuf scores;                      // plain form, per sorted position
+    cobs::DevBuf plain_part;                  // plain form: per-chunk counter sums of the column groups
+    cobs::DevBuf tickets;                     // plain form: per column group, chunks done
     cobs::DevBuf slices;
     uint32_t n_slices = 0, slice_lpq = 0;
     std::vector<uint32_t> block_slice0;       // per block: first slice (n_blocks + 1 entries)

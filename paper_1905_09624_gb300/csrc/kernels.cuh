@@ -138,39 +138,54 @@ void launch_gather_tma(const GatherArgs &a, uint32_t L, uint32_t grid, cudaStrea
 // spans a multiple of TERM_ALIGN slots (the gather reads row indices 16 at a time).
 constexpr uint64_t TERM_ALIGN = 16;
 
-// Plain form: one query, term chunks x 16-byte columns, partial scores by atomics.
-constexpr uint32_t PLAIN_CHUNK = 128;   // terms per chunk
-constexpr uint32_t PLAIN_THREADS = 128;
+// Plain form: one query per launch after its terms kernel, over tiles of
+// (128-byte column group of a block's rows) x (chunk of the query's terms); the
+// last tile of a column group adds the chunks' counts and thresholds.
+constexpr uint32_t PLAIN_WARPS = 4;
+constexpr uint32_t PLAIN_THREADS = PLAIN_WARPS * 32;
+constexpr uint32_t PLAIN_STREAMS = PLAIN_WARPS * 4;   // streams of 8 lanes per CTA
+constexpr uint32_t PLAIN_GROUP_BYTES = 128;           // a column group: 8 lanes x 16 bytes
+constexpr uint32_t PLAIN_MAX_CHUNKS = 64;
+constexpr uint32_t PLAIN_FUSED_MAX_H = 4;             // hashes of the fused form (its rows in shared memory)
 struct PlainArgs {
     const uint8_t *rows;
     const DevBlock *blocks;
-    const uint32_t *col_block;     // per 16-byte column (over all blocks): block index
-    const uint32_t *col_byte;      // per 16-byte column: byte offset within the row
-    uint32_t n_cols;
+    const SliceDesc *groups;       // column groups (block, byte offset), PLAIN_GROUP_BYTES wide
+    uint32_t n_groups;
+    uint32_t h;
+    const uint32_t *perm;          // sorted position -> original id
     const uint32_t *rows_idx;
     uint64_t tcap;
-    const uint64_t *term_base;     // of the query
-    const uint32_t *ell;           // of the query
-    uint32_t h;
-    uint32_t q;                    // query index (for term_base / ell)
-    uint32_t *scores;              // per sorted position, zeroed before
-};
-void launch_gather_plain(const PlainArgs &a, uint32_t n_chunks, cudaStream_t s);
-
-struct ThresholdArgs {
-    const uint32_t *scores;
-    const uint32_t *perm;
-    uint32_t n_docs;
-    const uint32_t *ell;
+    const uint64_t *term_base;     // two-kernel form: the terms kernel's regions
+    uint32_t *ell;                 // l per query (written by the fused form)
     const uint16_t *thr;
-    uint32_t q;
+    const uint8_t *bytes;          // fused form: the queries' bytes and n + 1 offsets
+    const uint64_t *offsets;
+    uint32_t kind, k;              // fused form: term kind and length
+    uint32_t q;                    // the query (index into offsets, term_base, ell, thr, qcount)
+    uint32_t n_chunks;             // grid.y; chunk c holds terms [c * chunk_terms, (c + 1) * chunk_terms)
+    uint32_t chunk_terms;          // a multiple of 16
+    uint32_t _pad;
+    uint32_t *partials;            // n_chunks > 1: [group][chunk][L][4][8] counter words
+    uint32_t *tickets;             // per group: chunks done; zero before the launch, zero after it
     unsigned long long *hit_count;
     uint32_t *qcount;
     uint32_t *raw_q;
     unsigned long long *raw_key;
     uint64_t hit_cap;
 };
-void launch_plain_threshold(const ThresholdArgs &a, cudaStream_t s);
+// Two-kernel form, after the terms kernel of the query (a programmatic dependent
+// of it).  L: counter levels, the query has fewer than 2^L terms.
+cudaError_t launch_plain_query(const PlainArgs &a, uint32_t L, cudaStream_t s);
+// Fused form (terms, gather, threshold in one launch) for a query of npos
+// windows; pdl: a programmatic dependent of the stream's previous kernel, which
+// must then be a plain kernel of the same stream or have completed the inputs.
+bool plain_fused_fits(uint64_t npos, uint32_t h);
+cudaError_t launch_plain_fused(const PlainArgs &a, uint32_t npos, bool pdl, cudaStream_t s);
+// Chunks (and terms per chunk) of a query of npos windows over n_groups column groups.
+uint32_t plain_chunks(uint64_t npos, uint32_t n_groups, uint32_t n_sm, uint32_t max_chunks, uint32_t *chunk_terms);
+// Words of the partials array for n_groups x n_chunks tiles (any L).
+uint64_t plain_partial_words(uint32_t n_groups, uint32_t n_chunks);
 
 // Hit finalisation: per-query offsets, scatter, sort (score desc, id asc), unpack.
 struct HitsArgs {

@@ -21,6 +21,12 @@ constexpr uint64_t NA_MAX_WINDOWS = COBS_NOALLOC_MAX_WINDOWS;
 constexpr uint64_t NA_MAX_DOCS = COBS_NOALLOC_MAX_DOCS;
 constexpr uint64_t NA_MAX_ROW_LISTS = COBS_NOALLOC_MAX_ROW_LISTS;
 constexpr uint64_t NA_TCAP = (NA_MAX_WINDOWS + TERM_ALIGN - 1) / TERM_ALIGN * TERM_ALIGN;
+// column groups of the plain kernel: one per 1,024 documents of a block, plus
+// one ragged group per block (blocks <= row lists)
+constexpr uint64_t NA_MAX_GROUPS = NA_MAX_DOCS / (PLAIN_GROUP_BYTES * 8) + NA_MAX_ROW_LISTS;
+constexpr uint32_t NA_MAX_CHUNKS = 4;  // term chunks of the plain kernel
+constexpr uint64_t NA_LEVELS = 16;      // counter levels: fewer than 2^16 terms
+static_assert(NA_MAX_WINDOWS < (1u << NA_LEVELS), "a query's counts fit NA_LEVELS levels");
 
 constexpr uint64_t al(uint64_t x) { return (x + 255) / 256 * 256; }
 
@@ -28,13 +34,14 @@ constexpr uint64_t al(uint64_t x) { return (x + 255) / 256 * 256; }
 constexpr uint64_t OFF_HDR = 0;                                          // offsets[2], term_base, table_base, thr
 constexpr uint64_t OFF_CTR = OFF_HDR + al(64);                           // qcount | counters (cleared per call)
 constexpr uint64_t CTR_BYTES = 256;
-constexpr uint64_t OFF_CURSOR = OFF_CTR + al(CTR_BYTES);                 // qcursor[1]
+constexpr uint64_t OFF_TICKETS = OFF_CTR + al(CTR_BYTES);                // per column group (cleared per call)
+constexpr uint64_t OFF_CURSOR = OFF_TICKETS + al(NA_MAX_GROUPS * 4);     // qcursor[1]
 constexpr uint64_t OFF_HITOFF = OFF_CURSOR + al(8);                      // hit_off[2]
 constexpr uint64_t OFF_ROWS = OFF_HITOFF + al(16);                       // row indices
 constexpr uint64_t OFF_CODES = OFF_ROWS + al(NA_MAX_ROW_LISTS * NA_TCAP * 4);
 constexpr uint64_t OFF_TABLE = OFF_CODES + al(NA_TCAP * 8);
-constexpr uint64_t OFF_SCORES = OFF_TABLE + al(2 * NA_MAX_WINDOWS * 8 + 128);
-constexpr uint64_t OFF_RAWQ = OFF_SCORES + al(NA_MAX_DOCS * 4);
+constexpr uint64_t OFF_PART = OFF_TABLE + al(2 * NA_MAX_WINDOWS * 8 + 128);  // plain kernel's chunk sums
+constexpr uint64_t OFF_RAWQ = OFF_PART + al(NA_MAX_GROUPS * NA_MAX_CHUNKS * NA_LEVELS * 32 * 4);
 constexpr uint64_t OFF_RAWKEY = OFF_RAWQ + al(NA_MAX_DOCS * 4);
 constexpr uint64_t OFF_KEYS = OFF_RAWKEY + al(NA_MAX_DOCS * 8);
 constexpr uint64_t OFF_TMP = OFF_KEYS + al(NA_MAX_DOCS * 8);
@@ -55,9 +62,12 @@ struct Header {
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 unsigned char *g_scratch[MAX_DEVICES] = {nullptr};
+int g_n_sm[MAX_DEVICES] = {0};
 
-// Device address of the scratch array on the current device (looked up once).
-cobs_status scratch_of(int dev, unsigned char **out) {
+// Device address of the scratch array on the current device and its SM count
+// (looked up once per device).  In host code g_noalloc_scratch names a host-side
+// stand-in, not the device array: only this address may be given to a kernel.
+cobs_status scratch_of(int dev, unsigned char **out, int *n_sm) {
     if (dev < 0 || dev >= MAX_DEVICES) return set_error(COBS_ERR_ARG, "device %d out of range", dev);
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_scratch[dev]) {
@@ -65,10 +75,32 @@ cobs_status scratch_of(int dev, unsigned char **out) {
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
             return set_error(COBS_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return set_error(COBS_ERR_CUDA, "SM count: %s", cudaGetErrorString(e));
+        g_n_sm[dev] = sms;
         g_scratch[dev] = static_cast<unsigned char *>(p);
     }
     *out = g_scratch[dev];
+    *n_sm = g_n_sm[dev];
     return COBS_OK;
+}
+
+// Per-call state, written on the device (no host buffer is read by the copy
+// engine): the query's offsets and threshold, zeroed counters and tickets.
+__global__ void k_noalloc_begin(unsigned char *S, uint64_t len, uint16_t thr, uint32_t n_tickets) {
+    if (threadIdx.x == 0) {
+        Header *h = reinterpret_cast<Header *>(S + OFF_HDR);
+        h->offsets[0] = 0;
+        h->offsets[1] = len;
+        h->term_base = 0;
+        h->table_base = 0;
+        h->thr = thr;
+    }
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(S + OFF_CTR);
+    for (uint32_t i = threadIdx.x; i < CTR_BYTES / 4; i += blockDim.x) ctr[i] = 0u;
+    uint32_t *tk = reinterpret_cast<uint32_t *>(S + OFF_TICKETS);
+    for (uint32_t i = threadIdx.x; i < n_tickets; i += blockDim.x) tk[i] = 0u;
 }
 
 }  // namespace
@@ -106,70 +138,72 @@ extern "C" cobs_status cobs_query_one_noalloc(cobs_device_index *dix, const uint
     int dev = 0;
     NA_CU(cudaGetDevice(&dev));
     if (dev != dix->device) return set_error(COBS_ERR_ARG, "current device %d is not the index's device %d", dev, dix->device);
+    if (dix->n_pgroups > NA_MAX_GROUPS)
+        return set_error(COBS_ERR_ARG, "index has %u column groups; this entry point takes at most %llu",
+                         dix->n_pgroups, (unsigned long long)NA_MAX_GROUPS);
     unsigned char *S = nullptr;
-    cobs_status st = scratch_of(dev, &S);
+    int n_sm = 0;
+    cobs_status st = scratch_of(dev, &S, &n_sm);
     if (st != COBS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
 
-    // per-call state: the query's offsets, thresholds, zeroed counters and scores
-    Header h;
-    memset(&h, 0, sizeof h);
-    h.offsets[1] = len;
-    h.thr = thr_permille;
-    NA_CU(cudaMemcpyAsync(S + OFF_HDR, &h, sizeof h, cudaMemcpyHostToDevice, s));
-    NA_CU(cudaMemsetAsync(S + OFF_CTR, 0, CTR_BYTES, s));
-    if (dix->n_docs) NA_CU(cudaMemsetAsync(S + OFF_SCORES, 0, dix->n_docs * 4, s));
+    k_noalloc_begin<<<1, 256, 0, s>>>(S, len, thr_permille, dix->n_pgroups);
+    NA_CU(cudaGetLastError());
     Header *dh = reinterpret_cast<Header *>(S + OFF_HDR);
     uint32_t *qcount = reinterpret_cast<uint32_t *>(S + OFF_CTR);
     unsigned long long *hit_count = reinterpret_cast<unsigned long long *>(S + OFF_CTR + 64);
 
-    TermsArgs ta{};
-    ta.bytes = query_dev;
-    ta.offsets = dh->offsets;
-    ta.term_base = &dh->term_base;
-    ta.table_base = &dh->table_base;
-    ta.tables = reinterpret_cast<unsigned long long *>(S + OFF_TABLE);
-    ta.ell = out_meta_dev;
-    ta.rows_idx = reinterpret_cast<uint32_t *>(S + OFF_ROWS);
-    ta.codes = reinterpret_cast<unsigned long long *>(S + OFF_CODES);
-    ta.tcap = NA_TCAP;
-    ta.blocks = dix->dblocks.as<DevBlock>();
-    ta.n_blocks = (uint32_t)dix->blocks.size();
-    ta.h = P.num_hashes;
-    ta.kind = P.term_kind;
-    ta.k = P.q;
-    ta.q0 = 0;
-    ta.smem_slots = TERMS_SMEM_SLOTS;
-    launch_query_terms(ta, 1, s);
-
     PlainArgs pa{};
     pa.rows = dix->dev_rows();
     pa.blocks = dix->dblocks.as<DevBlock>();
-    pa.col_block = dix->col_block.as<uint32_t>();
-    pa.col_byte = dix->col_byte.as<uint32_t>();
-    pa.n_cols = dix->n_cols;
-    pa.rows_idx = ta.rows_idx;
+    pa.groups = dix->pgroups.as<SliceDesc>();
+    pa.n_groups = dix->n_pgroups;
+    pa.h = P.num_hashes;
+    pa.perm = dix->dperm.as<uint32_t>();
+    pa.rows_idx = reinterpret_cast<uint32_t *>(S + OFF_ROWS);
     pa.tcap = NA_TCAP;
     pa.term_base = &dh->term_base;
     pa.ell = out_meta_dev;
-    pa.h = P.num_hashes;
+    pa.thr = &dh->thr;
+    pa.bytes = query_dev;
+    pa.offsets = dh->offsets;
+    pa.kind = P.term_kind;
+    pa.k = P.q;
     pa.q = 0;
-    pa.scores = reinterpret_cast<uint32_t *>(S + OFF_SCORES);
-    launch_gather_plain(pa, (uint32_t)((np + PLAIN_CHUNK - 1) / PLAIN_CHUNK), s);
-
-    ThresholdArgs th{};
-    th.scores = pa.scores;
-    th.perm = dix->dperm.as<uint32_t>();
-    th.n_docs = (uint32_t)dix->n_docs;
-    th.ell = out_meta_dev;
-    th.thr = &dh->thr;
-    th.q = 0;
-    th.hit_count = hit_count;
-    th.qcount = qcount;
-    th.raw_q = reinterpret_cast<uint32_t *>(S + OFF_RAWQ);
-    th.raw_key = reinterpret_cast<unsigned long long *>(S + OFF_RAWKEY);
-    th.hit_cap = NA_MAX_DOCS;
-    launch_plain_threshold(th, s);
+    pa.n_chunks = plain_chunks(np, dix->n_pgroups, (uint32_t)n_sm, NA_MAX_CHUNKS, &pa.chunk_terms);
+    pa.partials = reinterpret_cast<uint32_t *>(S + OFF_PART);
+    pa.tickets = reinterpret_cast<uint32_t *>(S + OFF_TICKETS);
+    pa.hit_count = hit_count;
+    pa.qcount = qcount;
+    pa.raw_q = reinterpret_cast<uint32_t *>(S + OFF_RAWQ);
+    pa.raw_key = reinterpret_cast<unsigned long long *>(S + OFF_RAWKEY);
+    pa.hit_cap = NA_MAX_DOCS;
+    const uint32_t levels = counter_levels_for((uint32_t)np);  // <= NA_LEVELS
+    if (plain_fused_fits(np, P.num_hashes)) {
+        // terms, gather and threshold in one launch; an ordinary launch, since it
+        // reads the offsets k_noalloc_begin wrote
+        NA_CU(launch_plain_fused(pa, (uint32_t)np, false, s));
+    } else {
+        TermsArgs ta{};
+        ta.bytes = query_dev;
+        ta.offsets = dh->offsets;
+        ta.term_base = &dh->term_base;
+        ta.table_base = &dh->table_base;
+        ta.tables = reinterpret_cast<unsigned long long *>(S + OFF_TABLE);
+        ta.ell = out_meta_dev;
+        ta.rows_idx = reinterpret_cast<uint32_t *>(S + OFF_ROWS);
+        ta.codes = reinterpret_cast<unsigned long long *>(S + OFF_CODES);
+        ta.tcap = NA_TCAP;
+        ta.blocks = dix->dblocks.as<DevBlock>();
+        ta.n_blocks = (uint32_t)dix->blocks.size();
+        ta.h = P.num_hashes;
+        ta.kind = P.term_kind;
+        ta.k = P.q;
+        ta.q0 = 0;
+        ta.smem_slots = TERMS_SMEM_SLOTS;
+        launch_query_terms(ta, 1, s);
+        NA_CU(launch_plain_query(pa, levels, s));
+    }
 
     HitsArgs ha{};
     ha.n_queries = 1;
@@ -181,8 +215,8 @@ extern "C" cobs_status cobs_query_one_noalloc(cobs_device_index *dix, const uint
     ha.hit_off = reinterpret_cast<uint64_t *>(S + OFF_HITOFF);
     ha.hit_count = hit_count;
     ha.hit_cap = NA_MAX_DOCS;
-    ha.raw_q = th.raw_q;
-    ha.raw_key = th.raw_key;
+    ha.raw_q = pa.raw_q;
+    ha.raw_key = pa.raw_key;
     ha.keys = reinterpret_cast<unsigned long long *>(S + OFF_KEYS);
     ha.tmp = reinterpret_cast<unsigned long long *>(S + OFF_TMP);
     ha.out_ids = out_ids_dev;

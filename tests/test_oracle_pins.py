@@ -40,6 +40,26 @@ def test_xxh64_spec_empty_input():
     assert oracle.xxh64(b"", 0) == 0xEF46DB3751D8E999
 
 
+def test_xxh64_known_answers_fixture():
+    # XXH64 answers written once by the reference xxHash library
+    # (tests/golden/make_xxh64_fixture.py): every length 0..72 (stripe loop and
+    # all tails), longer inputs and 8-byte term codes, five seeds.  Runs whether
+    # or not the library is installed here.
+    n = 0
+    for ln in open(os.path.join(GOLDEN, "xxh64_known_answers.txt")):
+        if ln.startswith("#") or not ln.strip():
+            continue
+        f = ln.split()
+        length, seed, want = int(f[0]), int(f[1]), int(f[2], 16)
+        data = bytes.fromhex(f[3]) if len(f) > 3 else b""
+        assert len(data) == length
+        assert oracle.xxh64(data, seed) == want, (length, seed)
+        if length == 8 and seed < 8:  # the hashed form of a term, seed = hash index
+            assert oracle.hash_term(int.from_bytes(data, "little"), seed) == want
+        n += 1
+    assert n >= 400
+
+
 def test_xxh64_against_libxxhash():
     lib = _libxxhash()
     if lib is None:
