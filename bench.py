@@ -56,6 +56,36 @@ def describe(wl, name):
             "thresholds_permille": sorted(set(int(t) for t in wl.thresholds))}
 
 
+def run_config(wl, name, world):
+    """The `config` object of the JSON line: the same keys and values in both
+    arms (the workload, how L2 is handled between GPU steps, the parallelism);
+    launch details of the GPU arm go to its `launch` object."""
+    return dict(describe(wl, name),
+                l2="GPU arm: a 512 MB write flushes L2 between timed steps, outside the timed events "
+                   "(the CPU reference arm has no GPU)",
+                parallelism=f"replicas x{world}" if world > 1 else "1 GPU")
+
+
+def l2_read_peak(cobs, torch, stream, nbytes=64 << 20, reps=150, trials=5):
+    """Read bandwidth of the L2 cache measured here: cobs_probe_l2_read over a
+    buffer well inside L2 (16-byte loads that bypass L1, a full grid), best of
+    `trials` launches after a warming one, CUDA events on the launching stream."""
+    buf = torch.ones(nbytes, dtype=torch.uint8, device="cuda")
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    best = 0.0
+    for t in range(trials + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cobs.probe_l2_read(buf.data_ptr(), nbytes, reps, sink.data_ptr(), 0, stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        if t:
+            best = max(best, nbytes * reps / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del buf, sink
+    return best
+
+
 class ClockSampler:
     """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -119,11 +149,11 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_record(kernel_srcs):
-    """The committed ncu record of the gather kernel on the bench workload (DRAM
-    bytes per launch, L2 figures), or None when the kernel's sources changed since
-    the counters were taken."""
-    p = os.path.join(ROOT, "profiles", "gather_batched_cfg2_dram.txt")
+def traffic_record(kernel_srcs, record="gather_batched_cfg2_dram.txt"):
+    """A committed ncu record of a gather kernel on a bench workload (DRAM bytes
+    per launch, L2 figures), or None when the kernel's sources changed since the
+    counters were taken."""
+    p = os.path.join(ROOT, "profiles", record)
     if not os.path.exists(p):
         return None
     kv = {}
@@ -210,8 +240,8 @@ def run_reference(args):
     value = sum(step_terms) / T
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / len(step_times),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-           "data": "synthetic", "config": describe(wl, args.config),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+           "data": "synthetic (seeded)", "config": run_config(wl, args.config, args.gpus),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"{per_step} queries per step, single thread, oracle index built untimed"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -234,11 +264,12 @@ def aggregate_over_ranks(seconds, units, dist=None, device="cpu"):
 
 
 # -------------------------------------------------------------------- serve
-def run_serve(dix, wl, rates, seconds, verify_oracle=None, inflight=3, wave_max=4096, workloads=None):
+def run_serve(dix, wl, rates, seconds, verify_oracle=None, inflight=3, wave_max=4096, workloads=None, form=0):
     """Poisson arrivals (cfg5 recipe on the given index) submitted at their
     arrival times from one thread, results polled from another; p50/p99 are the
-    library's submit-to-visible latencies.  Optionally checks a seeded 1% sample
-    of the results against the oracle index."""
+    library's submit-to-visible latencies.  form COBS_PLAIN: every wave is one
+    query in the plain form (the one-query-per-launch baseline).  Optionally
+    checks a seeded 1% sample of the results against the oracle index."""
     import synth
     from paper_1905_09624_gb300 import cobs
     out = []
@@ -247,7 +278,7 @@ def run_serve(dix, wl, rates, seconds, verify_oracle=None, inflight=3, wave_max=
         params = dict(synth.serving_params("cfg5", workloads), n_q=n, rate=rate)
         qb, qo, thr, src, t_arr = synth.config5_queries(wl, **params)
         ql = [bytes(qb[int(qo[i]):int(qo[i + 1])]) for i in range(n)]
-        srv = cobs.Server(dix, max_inflight_waves=inflight, max_wave_queries=wave_max)
+        srv = cobs.Server(dix, max_inflight_waves=inflight, max_wave_queries=wave_max, form=form)
         tickets = [None] * n
         results = [None] * n
         done_evt = threading.Event()
@@ -287,7 +318,8 @@ def run_serve(dix, wl, rates, seconds, verify_oracle=None, inflight=3, wave_max=
                "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "qps": stats["qps"],
                "kmers_per_s": terms / stats["seconds"] if stats["seconds"] else None,
                "mean_wave_queries": stats["mean_wave_queries"], "mean_wave_ms": stats["mean_wave_ms"],
-               "max_wave_ms": stats["max_wave_ms"], "inflight_waves": inflight}
+               "max_wave_ms": stats["max_wave_ms"], "inflight_waves": inflight,
+               "form": "plain (one query per wave and launch)" if form == cobs.COBS_PLAIN else "batched waves"}
         if verify_oracle is not None:
             # a seeded 1% sample of the requests, each an independent single-threaded
             # oracle query (run side by side on the host cores)
@@ -304,6 +336,136 @@ def run_serve(dix, wl, rates, seconds, verify_oracle=None, inflight=3, wave_max=
                 ok = sum(ex.map(same, sample.tolist()))
             rec["oracle_sample"] = f"{ok}/{len(sample)} identical"
         out.append(rec)
+    return out
+
+
+# ------------------------------------------------------------ other configs
+CONFIG_RECORDS = {  # committed ncu records of the gather on a config's full workload
+    "cfg4": ("gather_pipe_h3_cfg4_dram.txt", ["gather_h.cu", "gather_common.cuh"]),
+}
+PLAIN_SAMPLE = {"cfg1": 200, "cfg3": 1000, "cfg4": 10000}   # queries run in the plain form
+ORACLE_SAMPLE = {"cfg1": 200, "cfg4": 200}                 # queries compared with the oracle
+
+
+def _same_query(a, b, i, j):
+    """Query i of result arrays a equals query j of result arrays b."""
+    if a[0][i] != b[0][j] or a[1][i] != b[1][j]:
+        return False
+    sa = slice(int(a[2][i]), int(a[2][i + 1]))
+    sb = slice(int(b[2][j]), int(b[2][j + 1]))
+    return np.array_equal(a[3][sa], b[3][sb]) and np.array_equal(a[4][sa], b[4][sb])
+
+
+def measure_config(name, args, cobs, torch, stream, flush, device, hbm_peak, l2_peak):
+    """One more workload on this GPU: device build, the batched form as a
+    captured graph (L2 flushed between steps), the plain form on a sample of
+    its queries, and a sample compared with the oracle."""
+    wl = workload(name, args.workloads)
+    sh = stream.cuda_stream
+    P = cobs.make_params(**wl.params())
+    d_docs = torch.from_numpy(wl.docs).to("cuda")
+    d_doff = torch.from_numpy(wl.doc_off.view(np.int64)).to("cuda")
+    torch.cuda.synchronize()
+    build_ms = []
+    dix = None
+    for rep in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        dix = None
+        e0.record(stream)
+        dix = cobs.DeviceIndex.build_resident(P, d_docs, d_doff, wl.doc_off, stream=sh)
+        e1.record(stream)
+        e1.synchronize()
+        build_ms.append(e0.elapsed_time(e1))
+    del d_docs, d_doff
+    torch.cuda.empty_cache()
+    info = dix.info()
+    d_q = torch.from_numpy(wl.queries).to("cuda")
+    d_off = torch.from_numpy(wl.q_off.view(np.int64)).to("cuda")
+    d_thr = torch.from_numpy(wl.thresholds.view(np.int16)).to("cuda")
+    torch.cuda.synchronize()
+    eng = cobs.Engine(dix, stream=sh)
+    steps = args.cfg3_steps if name == "cfg3" else args.config_steps
+    ms, gms, terms, rows, launches = [], [], 0, 0, 0
+    for i in range(3 + steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        eng.query_device(d_q, d_off, wl.q_off, d_thr, cobs.COBS_GRAPH)
+        e1.record(stream)
+        st = eng.stats()
+        if i >= 3:
+            ms.append(e0.elapsed_time(e1))
+            gms.append(st["ms_gather"])
+            terms += st["terms"]
+            rows += st["row_bytes"]
+            launches += st["launches"]
+    batched = eng.download_arrays()
+    t_step = float(np.mean(ms)) / 1e3
+    g_step = float(np.mean(gms)) / 1e3
+    value = terms / steps / t_step
+    logical = rows / steps / g_step / 1e9
+    # the plain form on the first m queries, as its own batch
+    m = min(wl.n_queries, PLAIN_SAMPLE.get(name, 1000))
+    qo = wl.q_off[:m + 1].copy()
+    sub_q = torch.from_numpy(wl.queries[:int(qo[-1])]).to("cuda")
+    sub_off = torch.from_numpy(qo.view(np.int64)).to("cuda")
+    sub_thr = torch.from_numpy(wl.thresholds[:m].view(np.int16)).to("cuda")
+    torch.cuda.synchronize()
+    pms, pst = [], None
+    for rep in range(2):
+        with torch.cuda.stream(stream):
+            flush.fill_(rep)
+        eng.query_device(sub_q, sub_off, qo, sub_thr, cobs.COBS_PLAIN)
+        pst = eng.stats()
+        pms.append(pst["ms_total"])
+    plain_res = eng.download_arrays()
+    plain_same = all(_same_query(plain_res, batched, i, i) for i in range(m))
+    plain_value = pst["terms"] / (min(pms) / 1e3)
+    out = {"workload": describe(wl, name), "steps": steps, "warmup": 3, "form": "graph",
+           "value": value, "unit": UNIT, "ms_per_step": 1e3 * t_step, "gather_ms_per_step": 1e3 * g_step,
+           "gpu_launches_per_step": launches / steps,
+           "row_gbs_logical": logical, "row_frac_of_l2_peak": logical / l2_peak if l2_peak else None,
+           "reuse": logical / hbm_peak,
+           "plain": {"value": plain_value, "unit": UNIT, "queries": m, "ms": min(pms),
+                     "results_identical_to_batched": bool(plain_same)},
+           "speedup_batched_over_plain": value / plain_value if plain_value else None,
+           "build": {"ms_device": min(build_ms), "input_bytes": int(wl.doc_off[-1]),
+                     "gbs_device": int(wl.doc_off[-1]) / (min(build_ms) / 1e3) / 1e9,
+                     "index_bytes": info["rows_bytes"], "blocks": len(info["blocks"])}}
+    rec_name = CONFIG_RECORDS.get(name)
+    rec = None
+    if rec_name:
+        csrc = os.path.join(ROOT, "paper_1905_09624_gb300", "csrc")
+        rec = traffic_record([os.path.join(csrc, f) for f in rec_name[1]], rec_name[0])
+    out["row_gbs_physical"] = rec["dram_bytes"] / g_step / 1e9 if rec else None
+    out["physical_note"] = (f"ncu DRAM bytes of one launch (profiles/{rec_name[0]}) over the live gather time"
+                            if rec else "no current ncu record of this workload's gather")
+    del eng, sub_q, sub_off, sub_thr, d_q, d_off, d_thr
+    ns = ORACLE_SAMPLE.get(name, 0)
+    if ns and not args.skip_cpu:
+        import oracle
+        ix = oracle.build_index_threaded(oracle.make_params(**wl.params()), wl.docs, wl.doc_off)
+        ql = wl.query_list()
+        sample = np.random.default_rng(909).choice(wl.n_queries, min(ns, wl.n_queries), replace=False)
+        ok, t_cpu, cpu_terms = 0, 0.0, 0
+        for i in sample.tolist():
+            t0 = time.perf_counter()
+            ell, mn, ids, sc = ix.query(ql[i], int(wl.thresholds[i]))
+            t_cpu += time.perf_counter() - t0
+            cpu_terms += ell
+            h0, h1 = int(batched[2][i]), int(batched[2][i + 1])
+            ok += int(batched[0][i] == ell and batched[1][i] == mn and np.array_equal(batched[3][h0:h1], ids)
+                      and np.array_equal(batched[4][h0:h1], sc))
+        out["oracle_sample"] = f"{ok}/{len(sample)} identical (batched graph form vs the oracle)"
+        out["cpu_baseline"] = {"value": cpu_terms / t_cpu if t_cpu else None, "unit": UNIT, "cores": 1,
+                               "kind": "oracle", "sample": f"the same {len(sample)} queries, single thread"}
+        del ix
+    else:
+        out["oracle_sample"] = ("not run in the bench (the oracle's index of this workload takes minutes on the "
+                                "host cores); full-size parity is in tests/test_gpu_fullsize.py")
+    del dix, wl
+    torch.cuda.empty_cache()
     return out
 
 
@@ -406,6 +568,10 @@ def run_gpu(args):
     barrier()
     t_wall1 = time.time()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    # ---- the L2 read ceiling of the gather, measured now (clocks sampled meanwhile)
+    t_l2_0 = time.time()
+    l2_peak = l2_read_peak(cobs, torch, stream)
+    t_l2_1 = time.time()
     T, terms_all = aggregate_over_ranks(sum(step_ms) / 1e3, terms_total, dist, device="cuda")
     value = terms_all / T
 
@@ -573,30 +739,33 @@ def run_gpu(args):
     if rec and rec["slice_bytes"] != eng.stats()["slice_bytes"]:
         rec = None  # taken with another slice width
     kname = "k_gather_pipe" if wl.num_hashes == 1 else "k_gather_pipe_h" if wl.num_hashes <= 4 else "k_gather_batched"
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
-                "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                else "fallback", "unit": "GB/s", "frac": achieved / peak if achieved else None,
+    hbm_kind = (f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback")
+    # The gather reads every row slice of a batch through L2 many times (each
+    # distinct row once from HBM per residency): its logical row bytes are bound
+    # by the L2's read bandwidth, measured in this run; the DRAM side is the ncu
+    # traffic of the same launch over the live launch time.
+    dram_gbs = rec["dram_bytes"] / (g_ms / 1e3) / 1e9 if rec and g_ms > 0 else None
+    roofline = {"bound": "l2", "kernel": kname, "achieved": achieved, "peak": l2_peak, "unit": "GB/s",
+                "frac": achieved / l2_peak if achieved and l2_peak else None,
+                "peak_kind": "measured in this run: L2 read bandwidth (cobs_probe_l2_read: 64 MB buffer read "
+                             "150 times per launch, 16-byte L1-bypassing loads, best of 5 launches, CUDA events)",
                 "traffic": rec["dram_bytes"] if rec else None, "algorithmic_bytes_per_launch": alg_bytes,
                 "launch_ms": g_ms, "bytes_rule": "sum over distinct query terms and blocks of h * rowbytes_b",
-                # logical row bytes above the HBM peak come from reuse through L2,
-                # whose sector lookups are the binding unit (ncu, same workload)
+                "dram_gbs": dram_gbs, "dram_frac": dram_gbs / peak if dram_gbs else None,
+                "hbm_peak": peak, "hbm_peak_kind": hbm_kind,
+                "reuse": achieved / peak if achieved else None,
+                "reuse_rule": "logical row bytes per second over the HBM peak: above 1 only through L2 reuse",
                 "l2_hit_pct": rec["l2_hit_pct"] if rec else None,
-                "l2_sector_lookups_pct_of_peak": rec["l2_sector_lookups_pct_of_peak"] if rec else None}
-    if rec and g_ms > 0:
-        # the DRAM side of the same launch: the ncu traffic over the live launch time
-        dram_gbs = rec["dram_bytes"] / (g_ms / 1e3) / 1e9
-        roofline.update(dram_gbs=dram_gbs, dram_frac=dram_gbs / peak,
-                        binding_unit="L2 sector lookups (logical row bytes reach the SMs through L2; "
-                                     "frac > 1 is that reuse, not skipped work)")
+                "l2_sector_lookups_pct_of_peak": rec["l2_sector_lookups_pct_of_peak"] if rec else None,
+                "l2_probe_clocks": sampler.summary(t_l2_0, t_l2_1)}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded)",
-           "config": dict(describe(wl, args.config), form=args.form,
-                          l2="flushed between steps (512 MB write outside the timed events)",
-                          parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
-                          slice_bytes=eng.stats()["slice_bytes"], ctas_per_sm=eng.stats()["ctas_per_sm"],
-                          autotuned=tuned),
+           "config": run_config(wl, args.config, world),
+           "launch": {"form": args.form, "slice_bytes": eng.stats()["slice_bytes"],
+                      "ctas_per_sm": eng.stats()["ctas_per_sm"], "autotuned": tuned},
            "row_gbs_logical": row_bytes_total / T / 1e9,
            "roofline": roofline,
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -628,6 +797,15 @@ def run_gpu(args):
         out["serve"] = run_serve(dix, wl, rates, args.serve_seconds, verify_oracle=oracle_ix,
                                  inflight=args.serve_inflight, wave_max=args.serve_wave_max,
                                  workloads=args.workloads)
+        # the same arrivals served by the plain form: one query per wave and
+        # launch, one wave at a time
+        out["serve_plain"] = run_serve(dix, wl, rates, args.serve_seconds, verify_oracle=oracle_ix, inflight=1,
+                                       wave_max=1, workloads=args.workloads, form=cobs.COBS_PLAIN)
+    del dix, oracle_ix
+    if args.configs and world == 1:
+        out["configs"] = {}
+        for name in [c for c in args.configs.split(",") if c and c != args.config]:
+            out["configs"][name] = measure_config(name, args, cobs, torch, stream, flush, local, peak, l2_peak)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
@@ -671,6 +849,11 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=1.5)
     ap.add_argument("--serve-inflight", type=int, default=3, help="waves on the device at once")
     ap.add_argument("--serve-wave-max", type=int, default=4096, help="queries per wave at most")
+    ap.add_argument("--configs", default="cfg1,cfg4,cfg3",
+                    help="further workloads measured after the main one ('' to skip): batched graph form, "
+                         "plain form on a sample, device build, oracle sample")
+    ap.add_argument("--config-steps", type=int, default=10, help="timed steps of each further workload")
+    ap.add_argument("--cfg3-steps", type=int, default=3, help="timed steps of cfg3 (about 0.25 s each)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -190,6 +190,42 @@ cobs_status cobs_index_merge(const cobs_index *a, const cobs_index *b, cobs_inde
 cobs_status cobs_index_insert(const cobs_index *ix, const uint8_t *docs, const uint64_t *doc_offsets,
                               uint64_t n_docs, int device, cobs_index **out);
 
+/* ------------------------------------------------- sharding across devices */
+
+/* Document-block sharding (Sec. 4 names distributed query processing as future
+ * work; by Sec. 2.2 the blocks of a compact index are independent column groups
+ * and a document's score only involves its own block's rows, so whole blocks can
+ * sit on different devices and a query's hits are the union of the shards').
+ *
+ * cobs_shard_plan assigns every block of ix to one of n_shards shards, balancing
+ * the index bytes sum(w_b * rowbytes_b): blocks in decreasing order of bytes
+ * (ties: lower block first), each to the shard with the fewest bytes so far
+ * (ties: lower shard).  block_shard: n_blocks entries (host, caller-owned);
+ * shard_bytes (may be NULL): n_shards entries receiving each shard's bytes.
+ * Errors: ARG (n_shards 0 or above 65,536). */
+cobs_status cobs_shard_plan(const cobs_index *ix, uint32_t n_shards, uint32_t *block_shard, uint64_t *shard_bytes);
+
+/* The index of shard `shard` under block_shard: its blocks in their order with
+ * their rows byte for byte; its documents are those of its blocks, renumbered
+ * 0..n-1 in increasing order of their ids in ix (so a shard's hit order, by
+ * score then id, is the order of ix).  global_ids (may be NULL; capacity >=
+ * n_docs of ix) receives the id in ix of shard document j at [j]; *n_docs_out
+ * (may be NULL) = n.  A shard without blocks is an index of no documents.
+ * Host memory only; ix is unchanged.  Errors: ARG. */
+cobs_status cobs_index_shard(const cobs_index *ix, const uint32_t *block_shard, uint32_t shard, cobs_index **out,
+                             uint64_t *global_ids, uint64_t *n_docs_out);
+
+/* Merge one query's hit lists from n_shards shards into the order of the
+ * unsharded index: score descending, then id in ix ascending.  Shard s: n_hits[s]
+ * hits, ids[s] (shard-local ids) and scores[s] as a shard query returns them,
+ * global_ids[s] its id map (cobs_index_shard).  ids_out / scores_out: capacity
+ * sum(n_hits), receiving ids in ix and scores; *n_out = sum(n_hits).  l and
+ * ceil(K l) of a query are the same on every shard.  Host memory only.
+ * Errors: ARG (NULL arrays, an id beyond 32 bits). */
+cobs_status cobs_hits_merge(uint32_t n_shards, const uint32_t *const *ids, const uint32_t *const *scores,
+                            const uint64_t *n_hits, const uint64_t *const *global_ids, uint32_t *ids_out,
+                            uint32_t *scores_out, uint64_t *n_out);
+
 /* Inspect a host index.  Pointers stay valid until cobs_index_free.
  * perm[i] = original id of the document at sorted position i;
  * nterms[d] = distinct terms of original document d. */
@@ -323,7 +359,9 @@ typedef struct cobs_serve_cfg {
     uint32_t max_inflight_waves; /* waves on the device at once (0 = 2) */
     uint32_t max_wave_queries;   /* queries per wave (0 = 4096) */
     uint32_t wait_timeout_ms;    /* bounded waits for completions (0 = 10000) */
-    uint32_t _pad;
+    uint32_t form;               /* query form of every wave: 0 or COBS_BATCHED = one batched launch
+                                    sequence per wave; COBS_PLAIN = the plain form (one query per
+                                    launch; with max_wave_queries 1, one query per wave) */
 } cobs_serve_cfg;
 
 typedef struct cobs_serve_stats {

@@ -278,10 +278,9 @@ def plan(params: Params, v) -> Index:
     return Index(h.value)
 
 
-def build_index_threaded(params: Params, docs, doc_off, nthreads=None) -> Index:
-    """The same oracle functions as build_index, called on disjoint document and
-    column ranges from several Python threads (ctypes drops the GIL), so a large
-    oracle index is ready in seconds.  Each call is the single-threaded oracle."""
+def doc_counts_threaded(params: Params, docs, doc_off, nthreads=None):
+    """Distinct-term counts of every document: doc_counts on disjoint document
+    ranges from several Python threads (ctypes drops the GIL)."""
     from concurrent.futures import ThreadPoolExecutor
     n = len(doc_off) - 1
     nthreads = nthreads or os.cpu_count() or 1
@@ -292,14 +291,30 @@ def build_index_threaded(params: Params, docs, doc_off, nthreads=None) -> Index:
         for (a, b), res in zip(ranges, ex.map(lambda r: doc_counts(docs, doc_off, r[0], r[1],
                                                                    params.term_kind, params.q), ranges)):
             v[a:b] = res
-    ix = plan(params, v)
+    return v
+
+
+def fill_threaded(ix: Index, docs, doc_off, blocks=None, nthreads=None):
+    """Bloom bits of the given blocks (all by default): fill_columns on disjoint
+    column ranges (multiples of 8, so disjoint bytes) from several threads."""
+    from concurrent.futures import ThreadPoolExecutor
+    nthreads = nthreads or os.cpu_count() or 1
+    all_blocks = ix.blocks()
     jobs = []
-    for bi, blk in enumerate(ix.blocks()):
-        nb = blk["n_docs"]
+    for bi in (range(len(all_blocks)) if blocks is None else blocks):
+        nb = all_blocks[bi]["n_docs"]
         cstep = max(8, ((nb + 4 * nthreads - 1) // (4 * nthreads) + 7) // 8 * 8)
         jobs += [(bi, j, min(nb, j + cstep)) for j in range(0, nb, cstep)]
     with ThreadPoolExecutor(nthreads) as ex:
         list(ex.map(lambda jb: ix.fill_columns(docs, doc_off, *jb), jobs))
+
+
+def build_index_threaded(params: Params, docs, doc_off, nthreads=None) -> Index:
+    """The same oracle functions as build_index, called on disjoint document and
+    column ranges from several Python threads (ctypes drops the GIL), so a large
+    oracle index is ready in seconds.  Each call is the single-threaded oracle."""
+    ix = plan(params, doc_counts_threaded(params, docs, doc_off, nthreads))
+    fill_threaded(ix, docs, doc_off, None, nthreads)
     return ix
 
 

@@ -78,7 +78,7 @@ class cobs_query_stats(ctypes.Structure):
 class cobs_serve_cfg(ctypes.Structure):
     _fields_ = [("score_budget_bytes", ctypes.c_uint64), ("max_inflight_waves", ctypes.c_uint32),
                 ("max_wave_queries", ctypes.c_uint32), ("wait_timeout_ms", ctypes.c_uint32),
-                ("_pad", ctypes.c_uint32)]
+                ("form", ctypes.c_uint32)]
 
 
 class cobs_serve_stats(ctypes.Structure):
@@ -101,6 +101,9 @@ _PROTOS = {
     "cobs_multi_index_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_uint64, ctypes.POINTER(vp)]),
     "cobs_index_merge": (ctypes.c_int, [vp, vp, ctypes.POINTER(vp)]),
     "cobs_index_insert": (ctypes.c_int, [vp, vp, vp, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(vp)]),
+    "cobs_shard_plan": (ctypes.c_int, [vp, ctypes.c_uint32, vp, vp]),
+    "cobs_index_shard": (ctypes.c_int, [vp, vp, ctypes.c_uint32, ctypes.POINTER(vp), vp, u64p]),
+    "cobs_hits_merge": (ctypes.c_int, [ctypes.c_uint32, vp, vp, vp, vp, vp, vp, u64p]),
     "cobs_index_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
     "cobs_index_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(vp)]),
     "cobs_index_info": (ctypes.c_int, [vp, ctypes.POINTER(cobs_params), u64p, u64p,
@@ -310,6 +313,24 @@ class HostIndex(_Owned):
                                       device, ctypes.byref(h)), "cobs_index_insert")
         return HostIndex(h.value)
 
+    def shard_plan(self, n_shards):
+        """cobs_shard_plan: (block -> shard array, bytes per shard)."""
+        nb = len(self.info()["blocks"])
+        bs = np.zeros(max(nb, 1), np.uint32)
+        sb = np.zeros(n_shards, np.uint64)
+        check(lib().cobs_shard_plan(self.h, n_shards, _ptr(bs), _ptr(sb)), "cobs_shard_plan")
+        return bs[:nb], sb
+
+    def shard(self, block_shard, shard):
+        """cobs_index_shard: (shard index, ids in this index of its documents)."""
+        bs = np.ascontiguousarray(block_shard, dtype=np.uint32)
+        gids = np.zeros(max(self.info()["n_docs"], 1), np.uint64)
+        n = ctypes.c_uint64()
+        h = vp()
+        check(lib().cobs_index_shard(self.h, _ptr(bs), shard, ctypes.byref(h), _ptr(gids), ctypes.byref(n)),
+              "cobs_index_shard")
+        return HostIndex(h), gids[:n.value].copy()
+
     def merge(self, other):
         """cobs_index_merge: self's documents, then other's (ids shifted by self's count)."""
         h = vp()
@@ -480,11 +501,11 @@ class Server(_Owned):
     """cobs_server: continuous-batching serve loop."""
 
     def __init__(self, dix: DeviceIndex, score_budget_bytes=0, max_inflight_waves=0, max_wave_queries=0,
-                 wait_timeout_ms=0):
+                 wait_timeout_ms=0, form=0):
         self.dix = dix
         self._depends_on(dix)
         self._L = lib()
-        cfg = cobs_serve_cfg(score_budget_bytes, max_inflight_waves, max_wave_queries, wait_timeout_ms, 0)
+        cfg = cobs_serve_cfg(score_budget_bytes, max_inflight_waves, max_wave_queries, wait_timeout_ms, form)
         h = vp()
         check(self._L.cobs_serve_start(dix.h, ctypes.byref(cfg), ctypes.byref(h)), "cobs_serve_start")
         self.h = h
@@ -554,3 +575,22 @@ def debug_barrett_mod(x_ptr, n, w, out_ptr, stream=None):
     """cobs_debug_barrett_mod: out[i] = x[i] mod w on the device (pointers as integers)."""
     check(lib().cobs_debug_barrett_mod(ctypes.c_void_p(x_ptr), n, w, ctypes.c_void_p(out_ptr),
                                        ctypes.c_void_p(stream)), "cobs_debug_barrett_mod")
+
+
+def hits_merge(shard_hits, global_ids):
+    """cobs_hits_merge of one query: shard_hits[s] = (ids, scores) with
+    shard-local ids, global_ids[s] the shard's id map; returns (ids, scores)."""
+    n = len(shard_hits)
+    ids = [np.ascontiguousarray(h[0], dtype=np.uint32) for h in shard_hits]
+    sc = [np.ascontiguousarray(h[1], dtype=np.uint32) for h in shard_hits]
+    gid = [np.ascontiguousarray(g, dtype=np.uint64) for g in global_ids]
+    cnt = np.array([len(x) for x in ids], dtype=np.uint64)
+    total = int(cnt.sum())
+    P = ctypes.c_void_p * max(n, 1)
+    out_ids = np.zeros(max(total, 1), np.uint32)
+    out_sc = np.zeros(max(total, 1), np.uint32)
+    k = ctypes.c_uint64()
+    check(lib().cobs_hits_merge(n, P(*[x.ctypes.data for x in ids]), P(*[x.ctypes.data for x in sc]), _ptr(cnt),
+                                P(*[x.ctypes.data for x in gid]), _ptr(out_ids), _ptr(out_sc), ctypes.byref(k)),
+          "cobs_hits_merge")
+    return out_ids[:k.value].copy(), out_sc[:k.value].copy()

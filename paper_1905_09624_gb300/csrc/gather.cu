@@ -251,6 +251,15 @@ void launch_gather_batched_L(const GatherArgs &a, uint32_t lanes_per_query, uint
     }
 }
 
+// Warps per CTA of the batched kernel used for h hashes: the single-hash ring
+// PIPE_WARPS, the TMA feed and the multi-hash ring 2, the register kernel
+// GATHER_THREADS / 32.
+int gather_batched_warps_per_cta(uint32_t lanes_per_query, uint32_t h) {
+    if (h == 1) return PIPE_WARPS;
+    if (lanes_per_query == 8 && h <= 4) return 2;
+    return GATHER_THREADS / 32;
+}
+
 // Resident CTAs per SM of the batched kernel used for h hashes (persistent grid
 // = SMs x this).
 int gather_batched_max_blocks_per_sm(uint32_t lanes_per_query, uint32_t h) {

@@ -1263,7 +1263,8 @@ static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n
     // tiles hold, a multiple of TERM_ALIGN between SPLIT_MIN_TERMS and
     // SPLIT_TERMS.
     const uint64_t qpw = 32 / eng->lanes_per_query;
-    const uint64_t warps = (uint64_t)eng->n_sm * eng->ctas_per_sm * 2;
+    const uint64_t warps = (uint64_t)eng->n_sm * eng->ctas_per_sm *
+                           (uint64_t)gather_batched_warps_per_cta(eng->lanes_per_query, P.num_hashes);
     const bool small = (uint64_t)eng->n_slices * ((n + qpw - 1) / qpw) < 4 * warps;
     bool split = batched && P.num_hashes == 1 && eng->cfg.split != 1 && (eng->cfg.split == 2 || small);
     uint64_t part = SPLIT_TERMS;

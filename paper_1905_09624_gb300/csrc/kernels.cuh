@@ -130,6 +130,7 @@ void launch_gather_batched_L(const GatherArgs &a, uint32_t lanes_per_query, uint
                              cudaStream_t s);
 uint32_t counter_levels_for(uint32_t max_terms);
 int gather_batched_max_blocks_per_sm(uint32_t lanes_per_query, uint32_t h);
+int gather_batched_warps_per_cta(uint32_t lanes_per_query, uint32_t h);
 // the forms launch_gather_batched_L dispatches to (128-byte slices)
 void launch_gather_pipe_h(const GatherArgs &a, uint32_t L, uint32_t grid, cudaStream_t s);  // h = 2..4
 int gather_pipe_h_blocks_per_sm(uint32_t h);

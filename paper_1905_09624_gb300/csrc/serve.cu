@@ -27,7 +27,7 @@ struct CudaSlot {
 
 class CudaBackend final : public serve::Backend {
 public:
-    explicit CudaBackend(cobs_device_index *dix) : dix_(dix) {}
+    CudaBackend(cobs_device_index *dix, uint32_t flags) : dix_(dix), flags_(flags) {}
 
     ~CudaBackend() override {
         for (auto &sp : slots_) {
@@ -100,7 +100,7 @@ public:
             cudaMemcpyAsync(sl.dthr.p, pin + o2, n * 2, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
             return set_error(COBS_ERR_CUDA, "serve H2D");
         cobs_status st = engine_query(sl.eng, sl.dbytes.as<uint8_t>(), sl.doff.as<uint64_t>(), sl.hoff.data(),
-                                      sl.dthr.as<uint16_t>(), n, COBS_BATCHED);
+                                      sl.dthr.as<uint16_t>(), n, flags_);
         if (st != COBS_OK) return st;
         if (cudaEventRecord(sl.done, sl.stream) != cudaSuccess) return set_error(COBS_ERR_CUDA, "serve event");
         sl.n = n;
@@ -142,6 +142,7 @@ public:
 
 private:
     cobs_device_index *dix_;
+    uint32_t flags_;  // COBS_BATCHED or COBS_PLAIN
     std::vector<std::unique_ptr<CudaSlot>> slots_;
 };
 
@@ -150,7 +151,11 @@ private:
 extern "C" cobs_status cobs_serve_start(cobs_device_index *dix, const cobs_serve_cfg *cfg, cobs_server **out) {
     if (!dix || !out) return set_error(COBS_ERR_ARG, "NULL argument");
     if (cudaSetDevice(dix->device) != cudaSuccess) return set_error(COBS_ERR_CUDA, "cudaSetDevice");
-    std::unique_ptr<CudaBackend> be(new CudaBackend(dix));
+    const uint32_t form = cfg ? cfg->form : 0u;
+    if (form != 0u && form != COBS_BATCHED && form != COBS_PLAIN)
+        return set_error(COBS_ERR_ARG, "serve form must be 0, COBS_BATCHED or COBS_PLAIN");
+    if (form == COBS_PLAIN && dix->streamed) return set_error(COBS_ERR_ARG, "the plain form needs a resident index");
+    std::unique_ptr<CudaBackend> be(new CudaBackend(dix, form == COBS_PLAIN ? COBS_PLAIN : COBS_BATCHED));
     const uint32_t n_slots = cfg && cfg->max_inflight_waves ? cfg->max_inflight_waves : 2;
     cobs_status st = be->init(n_slots);
     if (st != COBS_OK) return st;

@@ -55,6 +55,25 @@ def test_serve_matches_oracle_and_batched(served):
         assert a[0] == b[0] and a[1] == b[1] and np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
 
 
+def test_serve_plain_form_matches_oracle(served):
+    # waves of one query in the plain form (the one-query-per-launch baseline of
+    # the serving comparison): the same results as the oracle
+    wl, ref, dix = served
+    ql = wl.query_list()
+    srv = cobs.Server(dix, max_inflight_waves=1, max_wave_queries=1, form=cobs.COBS_PLAIN)
+    tickets = [srv.submit(q, int(wl.thresholds[i])) for i, q in enumerate(ql)]
+    got = _wait(srv, tickets)
+    stats = srv.stop()
+    assert stats["completed"] == len(ql) and stats["waves"] == len(ql)
+    assert_results_equal(got, ref, ql, wl.thresholds)
+
+
+def test_serve_rejects_unknown_form(served):
+    _, _, dix = served
+    with pytest.raises(cobs.CobsError):
+        cobs.Server(dix, form=7)
+
+
 def test_same_result_alone_and_mixed_under_load(served):
     wl, ref, dix = served
     ql = wl.query_list()
