@@ -263,6 +263,32 @@ def aggregate_over_ranks(seconds, units, dist=None, device="cpu"):
     return float(t.item()), float(u.item())
 
 
+# ------------------------------------------------------------------ sharding
+def gather_id_maps(gids, dist):
+    """Every rank's shard id map, on rank 0 (None elsewhere); once per run."""
+    if dist is None:
+        return [gids]
+    parts = [None] * dist.get_world_size() if dist.get_rank() == 0 else None
+    dist.gather_object(gids, parts, dst=0)
+    return parts
+
+
+def exchange_and_merge(res, id_maps, dist):
+    """The exchange step of the sharded path: every rank's hit lists of a batch
+    (hit_offsets, shard-local ids, scores) go to rank 0, which merges them into
+    the order of the unsharded index (cobs_hits_merge).  Returns the merged
+    (hit_offsets, ids, scores) on rank 0, None elsewhere."""
+    from paper_1905_09624_gb300 import cobs
+    if dist is None:
+        parts = [res]
+    else:
+        parts = [None] * dist.get_world_size() if dist.get_rank() == 0 else None
+        dist.gather_object(res, parts, dst=0)
+        if dist.get_rank() != 0:
+            return None
+    return cobs.hits_merge(parts, id_maps)
+
+
 # -------------------------------------------------------------------- serve
 def run_serve(dix, wl, rates, seconds, verify_oracle=None, inflight=3, wave_max=4096, workloads=None, form=0):
     """Poisson arrivals (cfg5 recipe on the given index) submitted at their
@@ -384,6 +410,11 @@ def measure_config(name, args, cobs, torch, stream, flush, device, hbm_peak, l2_
     d_thr = torch.from_numpy(wl.thresholds.view(np.int16)).to("cuda")
     torch.cuda.synchronize()
     eng = cobs.Engine(dix, stream=sh)
+    tuned = None
+    if name in [c for c in args.autotune_configs.split(",") if c]:
+        t0 = time.perf_counter()
+        tuned = eng.autotune(d_q, d_off, wl.q_off, d_thr)
+        tuned["seconds"] = time.perf_counter() - t0
     steps = args.cfg3_steps if name == "cfg3" else args.config_steps
     ms, gms, terms, rows, launches = [], [], 0, 0, 0
     for i in range(3 + steps):
@@ -422,7 +453,9 @@ def measure_config(name, args, cobs, torch, stream, flush, device, hbm_peak, l2_
     plain_res = eng.download_arrays()
     plain_same = all(_same_query(plain_res, batched, i, i) for i in range(m))
     plain_value = pst["terms"] / (min(pms) / 1e3)
+    st = eng.stats()
     out = {"workload": describe(wl, name), "steps": steps, "warmup": 3, "form": "graph",
+           "launch": {"slice_bytes": st["slice_bytes"], "ctas_per_sm": st["ctas_per_sm"], "autotuned": tuned},
            "value": value, "unit": UNIT, "ms_per_step": 1e3 * t_step, "gather_ms_per_step": 1e3 * g_step,
            "gpu_launches_per_step": launches / steps,
            "row_gbs_logical": logical, "row_frac_of_l2_peak": logical / l2_peak if l2_peak else None,
@@ -467,6 +500,83 @@ def measure_config(name, args, cobs, torch, stream, flush, device, hbm_peak, l2_
     del dix, wl
     torch.cuda.empty_cache()
     return out
+
+
+# --------------------------------------------------------------- sharded GPU
+def run_gpu_sharded(args):
+    """--shard: document-block sharding over the ranks (one GPU each).  Every
+    rank builds the index, keeps the blocks of its shard (cobs_shard_plan /
+    cobs_index_shard) and answers every query of the batch over its documents
+    (graph form); a step ends with the exchange: the ranks' hit lists to rank 0,
+    merged into the order of the unsharded index.  The batch and the index are
+    fixed as N grows ("scaling": "strong"); value = distinct query terms of the
+    batch (each over the whole index) / the slowest rank's step time."""
+    import torch
+    from paper_1905_09624_gb300 import cobs
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the CUDA library has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wl = workload(args.config, args.workloads)
+    stream = torch.cuda.Stream()
+    P = cobs.make_params(**wl.params())
+    host = cobs.DeviceIndex.build(P, wl.docs, wl.doc_off, device=local).download()
+    plan, shard_bytes = host.shard_plan(world)
+    sub, gids = host.shard(plan, rank)
+    sdix = cobs.DeviceIndex.load(sub, device=local)
+    del host
+    maps = gather_id_maps(gids, dist)
+    eng = cobs.Engine(sdix, stream=stream.cuda_stream)
+    d_q = torch.from_numpy(wl.queries).to("cuda")
+    d_off = torch.from_numpy(wl.q_off.view(np.int64)).to("cuda")
+    d_thr = torch.from_numpy(wl.thresholds.view(np.int16)).to("cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        with torch.cuda.stream(stream):
+            flush.fill_(rank + 1)
+        eng.query_device(d_q, d_off, wl.q_off, d_thr, cobs.COBS_GRAPH)
+        res = eng.download_arrays()
+        merged = exchange_and_merge((res[2], res[3], res[4]), maps, dist)
+        return res, merged
+
+    for _ in range(args.warmup):
+        step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    terms = 0
+    for _ in range(args.steps):
+        res, merged = step()
+        terms += int(np.sum(res[0]))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    dt = time.perf_counter() - t0
+    T, _ = aggregate_over_ranks(dt, terms, dist, device="cuda")
+    if rank == 0:
+        out = {"metric": METRIC + ", document blocks sharded over the GPUs", "value": terms / T, "unit": UNIT,
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+               "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u32",
+               "data": "synthetic (seeded)", "config": dict(run_config(wl, args.config, world),
+                                                            parallelism=f"document-block shards x{world}"),
+               "shards": {"block_shard": plan.tolist(), "shard_bytes": shard_bytes.tolist(),
+                          "exchange": "hit lists gathered to rank 0 (gather_object), cobs_hits_merge",
+                          "hits_per_step": int(merged[0][-1])},
+               "timing": "wall clock per step (query, hit download, exchange, merge), barriers on both sides, "
+                         "max over ranks"}
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
 
 
 # ---------------------------------------------------------------------- GPU
@@ -849,16 +959,22 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=1.5)
     ap.add_argument("--serve-inflight", type=int, default=3, help="waves on the device at once")
     ap.add_argument("--serve-wave-max", type=int, default=4096, help="queries per wave at most")
+    ap.add_argument("--shard", action="store_true",
+                    help="document-block sharding over the ranks instead of replicas (strong scaling)")
     ap.add_argument("--configs", default="cfg1,cfg4,cfg3",
                     help="further workloads measured after the main one ('' to skip): batched graph form, "
                          "plain form on a sample, device build, oracle sample")
     ap.add_argument("--config-steps", type=int, default=10, help="timed steps of each further workload")
+    ap.add_argument("--autotune-configs", default="cfg3",
+                    help="further workloads whose engine is autotuned on their batch before the timed steps")
     ap.add_argument("--cfg3-steps", type=int, default=3, help="timed steps of cfg3 (about 0.25 s each)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.shard:
+        return run_gpu_sharded(args)
     return run_gpu(args)
 
 

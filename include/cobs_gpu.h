@@ -215,16 +215,19 @@ cobs_status cobs_shard_plan(const cobs_index *ix, uint32_t n_shards, uint32_t *b
 cobs_status cobs_index_shard(const cobs_index *ix, const uint32_t *block_shard, uint32_t shard, cobs_index **out,
                              uint64_t *global_ids, uint64_t *n_docs_out);
 
-/* Merge one query's hit lists from n_shards shards into the order of the
- * unsharded index: score descending, then id in ix ascending.  Shard s: n_hits[s]
- * hits, ids[s] (shard-local ids) and scores[s] as a shard query returns them,
- * global_ids[s] its id map (cobs_index_shard).  ids_out / scores_out: capacity
- * sum(n_hits), receiving ids in ix and scores; *n_out = sum(n_hits).  l and
- * ceil(K l) of a query are the same on every shard.  Host memory only.
- * Errors: ARG (NULL arrays, an id beyond 32 bits). */
-cobs_status cobs_hits_merge(uint32_t n_shards, const uint32_t *const *ids, const uint32_t *const *scores,
-                            const uint64_t *n_hits, const uint64_t *const *global_ids, uint32_t *ids_out,
-                            uint32_t *scores_out, uint64_t *n_out);
+/* Merge the hit lists of n_queries queries from n_shards shards into the order
+ * of the unsharded index: per query, score descending, then id in ix ascending.
+ * Shard s gives its results as a shard query returns them: hit_offsets[s]
+ * (n_queries + 1 offsets), ids[s] (shard-local ids) and scores[s], with
+ * global_ids[s] its id map (cobs_index_shard).  Output: hit_offsets_out
+ * (n_queries + 1, starting at 0), ids_out (ids in ix) and scores_out, each of
+ * capacity sum over shards of their hits.  l and ceil(K l) of a query are the
+ * same on every shard.  Host memory only.  Errors: ARG (NULL arrays, decreasing
+ * offsets, an id beyond 32 bits). */
+cobs_status cobs_hits_merge(uint32_t n_shards, uint64_t n_queries, const uint64_t *const *hit_offsets,
+                            const uint32_t *const *ids, const uint32_t *const *scores,
+                            const uint64_t *const *global_ids, uint64_t *hit_offsets_out, uint32_t *ids_out,
+                            uint32_t *scores_out);
 
 /* Inspect a host index.  Pointers stay valid until cobs_index_free.
  * perm[i] = original id of the document at sorted position i;
@@ -285,7 +288,14 @@ typedef struct cobs_engine_cfg {
                                  index: 0 = default, 1 = cp.async ring (16-byte pieces per
                                  lane), 2 = TMA gather (tile::gather4, four indexed rows per
                                  copy, one tensor map per block); others use the ring */
-    uint32_t _pad2;
+    uint32_t split_part;      /* terms per part of a split query (the query-term chunk of a
+                                 work tile): 0 = sized per batch (see split); else a multiple
+                                 of 16 in 256..4080 */
+    uint32_t class_streams;   /* counter classes of a batch (queries grouped by length): 0 or 1 =
+                                 each class's gather on a stream of its own, overlapping;
+                                 2 = all on the engine stream, one after another */
+    uint32_t tuned_from_cache;/* cobs_engine_autotune output: 1 when the choice came from the
+                                 process-wide cache of earlier sweeps (ignored on input) */
 } cobs_engine_cfg;
 
 cobs_status cobs_engine_create(cobs_device_index *dix, const cobs_engine_cfg *cfg, void *stream,
@@ -344,10 +354,18 @@ typedef struct cobs_query_stats {
 } cobs_query_stats;
 cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out);
 
-/* Autotune the batched kernel's slice width, resident CTAs per SM and L2
- * hints on a sample batch (device inputs as in cobs_engine_query_device): each
- * shape's gather is timed from a cold L2, best of repeats; the fastest is kept
- * by the engine.  Writes the chosen values to cfg_out. */
+/* Autotune the batched form's work tiles on a sample batch (device inputs as in
+ * cobs_engine_query_device; Sec. 2.3 scores documents in parallel partitions,
+ * here tiles of a row slice x a chunk of a query's terms).  Dimensions, swept one
+ * after another from the engine's current choice (coordinate descent): slice
+ * width, resident CTAs per SM, L2 hints, the query-term chunk (split: none, the
+ * batch-sized part, parts of 4,080 and 1,024 terms; single-hash indexes), and the
+ * counter-class streams (overlapping or serial).  Each candidate runs the whole
+ * batch from a cold L2, best of two; the fastest by the time of its kernels
+ * (terms to hits) is kept by the engine and written to cfg_out.  The choice is
+ * cached process-wide under the index's block shape and the batch's
+ * query-length histogram (log2 buckets); a later call with the same key applies
+ * the cached choice without sweeping (cfg_out->tuned_from_cache = 1). */
 cobs_status cobs_engine_autotune(cobs_engine *eng, const uint8_t *queries_dev, const uint64_t *offsets_dev,
                                  const uint64_t *offsets_host, const uint16_t *thr_dev, uint64_t n,
                                  cobs_engine_cfg *cfg_out);
@@ -461,7 +479,7 @@ const char *cobs_version(void);
 /* Version of this header's types and entry points; it changes whenever a struct
  * layout or a signature changes.  A caller built against this header checks
  * cobs_abi_version() == COBS_GPU_ABI_VERSION before using the library. */
-#define COBS_GPU_ABI_VERSION 3u
+#define COBS_GPU_ABI_VERSION 4u
 uint32_t cobs_abi_version(void);
 
 /* Host-side fault injection for tests (the paper has no counterpart).  After

@@ -26,7 +26,7 @@ COBS_ERR_OVERFLOW = -7
 COBS_ERR_NOT_FOUND = -8
 COBS_ERR_CANCELLED = -9
 
-ABI_VERSION = 3  # COBS_GPU_ABI_VERSION of include/cobs_gpu.h that the structs below mirror
+ABI_VERSION = 4  # COBS_GPU_ABI_VERSION of include/cobs_gpu.h that the structs below mirror
 
 COBS_PLAIN = 1
 COBS_BATCHED = 2
@@ -63,7 +63,8 @@ class cobs_engine_cfg(ctypes.Structure):
     _fields_ = [("max_queries", ctypes.c_uint64), ("max_query_bytes", ctypes.c_uint64), ("max_hits", ctypes.c_uint64),
                 ("slice_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("l2_hints", ctypes.c_uint32),
                 ("split", ctypes.c_uint32), ("stage_bytes", ctypes.c_uint64), ("gather_feed", ctypes.c_uint32),
-                ("_pad2", ctypes.c_uint32)]
+                ("split_part", ctypes.c_uint32), ("class_streams", ctypes.c_uint32),
+                ("tuned_from_cache", ctypes.c_uint32)]
 
 
 class cobs_query_stats(ctypes.Structure):
@@ -103,7 +104,7 @@ _PROTOS = {
     "cobs_index_insert": (ctypes.c_int, [vp, vp, vp, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(vp)]),
     "cobs_shard_plan": (ctypes.c_int, [vp, ctypes.c_uint32, vp, vp]),
     "cobs_index_shard": (ctypes.c_int, [vp, vp, ctypes.c_uint32, ctypes.POINTER(vp), vp, u64p]),
-    "cobs_hits_merge": (ctypes.c_int, [ctypes.c_uint32, vp, vp, vp, vp, vp, vp, u64p]),
+    "cobs_hits_merge": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, vp, vp, vp, vp, vp, vp, vp]),
     "cobs_index_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
     "cobs_index_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(vp)]),
     "cobs_index_info": (ctypes.c_int, [vp, ctypes.POINTER(cobs_params), u64p, u64p,
@@ -329,7 +330,7 @@ class HostIndex(_Owned):
         h = vp()
         check(lib().cobs_index_shard(self.h, _ptr(bs), shard, ctypes.byref(h), _ptr(gids), ctypes.byref(n)),
               "cobs_index_shard")
-        return HostIndex(h), gids[:n.value].copy()
+        return HostIndex(h.value), gids[:n.value].copy()
 
     def merge(self, other):
         """cobs_index_merge: self's documents, then other's (ids shifted by self's count)."""
@@ -424,10 +425,11 @@ class Engine(_Owned):
     """cobs_engine: reusable query workspace on one device index."""
 
     def __init__(self, dix: DeviceIndex, stream=None, slice_bytes=0, ctas_per_sm=0, max_hits=0, l2_hints=0, split=0,
-                 stage_bytes=0, gather_feed=0):
+                 stage_bytes=0, gather_feed=0, split_part=0, class_streams=0):
         self.dix = dix
         self._depends_on(dix)
-        cfg = cobs_engine_cfg(0, 0, max_hits, slice_bytes, ctas_per_sm, l2_hints, split, stage_bytes, gather_feed, 0)
+        cfg = cobs_engine_cfg(0, 0, max_hits, slice_bytes, ctas_per_sm, l2_hints, split, stage_bytes, gather_feed,
+                              split_part, class_streams, 0)
         h = vp()
         check(lib().cobs_engine_create(dix.h, ctypes.byref(cfg), stream, ctypes.byref(h)), "cobs_engine_create")
         self.h = h
@@ -494,7 +496,9 @@ class Engine(_Owned):
         cfg = cobs_engine_cfg()
         check(lib().cobs_engine_autotune(self.h, _ptr(q_dev), _ptr(off_dev), _ptr(off_host), _ptr(thr_dev),
                                          len(off_host) - 1, ctypes.byref(cfg)), "cobs_engine_autotune")
-        return dict(slice_bytes=cfg.slice_bytes, ctas_per_sm=cfg.ctas_per_sm, l2_hints=cfg.l2_hints)
+        return dict(slice_bytes=cfg.slice_bytes, ctas_per_sm=cfg.ctas_per_sm, l2_hints=cfg.l2_hints, split=cfg.split,
+                    split_part=cfg.split_part, class_streams=cfg.class_streams,
+                    from_cache=bool(cfg.tuned_from_cache))
 
 
 class Server(_Owned):
@@ -577,20 +581,22 @@ def debug_barrett_mod(x_ptr, n, w, out_ptr, stream=None):
                                        ctypes.c_void_p(stream)), "cobs_debug_barrett_mod")
 
 
-def hits_merge(shard_hits, global_ids):
-    """cobs_hits_merge of one query: shard_hits[s] = (ids, scores) with
-    shard-local ids, global_ids[s] the shard's id map; returns (ids, scores)."""
-    n = len(shard_hits)
-    ids = [np.ascontiguousarray(h[0], dtype=np.uint32) for h in shard_hits]
-    sc = [np.ascontiguousarray(h[1], dtype=np.uint32) for h in shard_hits]
+def hits_merge(shard_results, global_ids):
+    """cobs_hits_merge of a batch: shard_results[s] = (hit_offsets, ids, scores)
+    with shard-local ids (e.g. from download_arrays), global_ids[s] the shard's
+    id map; returns (hit_offsets, ids, scores) in the order of the unsharded index."""
+    n = len(shard_results)
+    offs = [np.ascontiguousarray(r[0], dtype=np.uint64) for r in shard_results]
+    ids = [np.ascontiguousarray(r[1], dtype=np.uint32) for r in shard_results]
+    sc = [np.ascontiguousarray(r[2], dtype=np.uint32) for r in shard_results]
     gid = [np.ascontiguousarray(g, dtype=np.uint64) for g in global_ids]
-    cnt = np.array([len(x) for x in ids], dtype=np.uint64)
-    total = int(cnt.sum())
+    nq = len(offs[0]) - 1 if n else 0
+    total = sum(int(o[-1] - o[0]) for o in offs)
     P = ctypes.c_void_p * max(n, 1)
+    out_off = np.zeros(nq + 1, np.uint64)
     out_ids = np.zeros(max(total, 1), np.uint32)
     out_sc = np.zeros(max(total, 1), np.uint32)
-    k = ctypes.c_uint64()
-    check(lib().cobs_hits_merge(n, P(*[x.ctypes.data for x in ids]), P(*[x.ctypes.data for x in sc]), _ptr(cnt),
-                                P(*[x.ctypes.data for x in gid]), _ptr(out_ids), _ptr(out_sc), ctypes.byref(k)),
-          "cobs_hits_merge")
-    return out_ids[:k.value].copy(), out_sc[:k.value].copy()
+    check(lib().cobs_hits_merge(n, nq, P(*[x.ctypes.data for x in offs]), P(*[x.ctypes.data for x in ids]),
+                                P(*[x.ctypes.data for x in sc]), P(*[x.ctypes.data for x in gid]), _ptr(out_off),
+                                _ptr(out_ids), _ptr(out_sc)), "cobs_hits_merge")
+    return out_off, out_ids[:total].copy(), out_sc[:total].copy()

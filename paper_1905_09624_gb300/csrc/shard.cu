@@ -87,19 +87,23 @@ extern "C" cobs_status cobs_index_shard(const cobs_index *ix, const uint32_t *bl
     return COBS_OK;
 }
 
-// k-way merge by (score descending, id in ix ascending).  Each shard's list is
-// already in that order: its local ids increase with the ids in ix.
-extern "C" cobs_status cobs_hits_merge(uint32_t n_shards, const uint32_t *const *ids, const uint32_t *const *scores,
-                                       const uint64_t *n_hits, const uint64_t *const *global_ids, uint32_t *ids_out,
-                                       uint32_t *scores_out, uint64_t *n_out) {
-    if (!n_hits || !n_out || (n_shards && (!ids || !scores || !global_ids)))
+// k-way merge by (score descending, id in ix ascending), query by query.  Each
+// shard's list of a query is already in that order: its local ids increase
+// with the ids in ix.
+extern "C" cobs_status cobs_hits_merge(uint32_t n_shards, uint64_t n_queries, const uint64_t *const *hit_offsets,
+                                       const uint32_t *const *ids, const uint32_t *const *scores,
+                                       const uint64_t *const *global_ids, uint64_t *hit_offsets_out,
+                                       uint32_t *ids_out, uint32_t *scores_out) {
+    if (!hit_offsets_out || (n_shards && (!hit_offsets || !ids || !scores || !global_ids)))
         return set_error(COBS_ERR_ARG, "NULL argument");
     if (n_shards > MAX_SHARDS) return set_error(COBS_ERR_ARG, "n_shards must be at most 65536");
     uint64_t total = 0;
     for (uint32_t s = 0; s < n_shards; s++) {
-        if (n_hits[s] && (!ids[s] || !scores[s] || !global_ids[s]))
+        if (!hit_offsets[s]) return set_error(COBS_ERR_ARG, "NULL hit offsets of shard %u", s);
+        const uint64_t n = hit_offsets[s][n_queries] - hit_offsets[s][0];
+        if (n && (!ids[s] || !scores[s] || !global_ids[s]))
             return set_error(COBS_ERR_ARG, "NULL hit list of shard %u", s);
-        total += n_hits[s];
+        total += n;
     }
     if (total && (!ids_out || !scores_out)) return set_error(COBS_ERR_ARG, "NULL output");
     struct Head {
@@ -110,21 +114,30 @@ extern "C" cobs_status cobs_hits_merge(uint32_t n_shards, const uint32_t *const 
     auto after = [](const Head &a, const Head &b) {  // a comes after b in the merged order
         return a.score != b.score ? a.score < b.score : a.id > b.id;
     };
-    std::priority_queue<Head, std::vector<Head>, decltype(after)> heap(after);
-    std::vector<uint64_t> pos(n_shards, 0);
-    for (uint32_t s = 0; s < n_shards; s++)
-        if (n_hits[s]) heap.push(Head{scores[s][0], global_ids[s][ids[s][0]], s});
+    std::vector<Head> store;
+    store.reserve(n_shards);
+    std::priority_queue<Head, std::vector<Head>, decltype(after)> heap(after, std::move(store));
+    std::vector<uint64_t> pos(n_shards, 0), end(n_shards, 0);
     uint64_t k = 0;
-    while (!heap.empty()) {
-        const Head h = heap.top();
-        heap.pop();
-        if (h.id > 0xFFFFFFFFULL) return set_error(COBS_ERR_ARG, "document id beyond 32 bits");
-        ids_out[k] = (uint32_t)h.id;
-        scores_out[k] = h.score;
-        k++;
-        const uint64_t p = ++pos[h.shard];
-        if (p < n_hits[h.shard]) heap.push(Head{scores[h.shard][p], global_ids[h.shard][ids[h.shard][p]], h.shard});
+    hit_offsets_out[0] = 0;
+    for (uint64_t q = 0; q < n_queries; q++) {
+        for (uint32_t s = 0; s < n_shards; s++) {
+            pos[s] = hit_offsets[s][q];
+            end[s] = hit_offsets[s][q + 1];
+            if (end[s] < pos[s]) return set_error(COBS_ERR_ARG, "hit offsets of shard %u decrease", s);
+            if (pos[s] < end[s]) heap.push(Head{scores[s][pos[s]], global_ids[s][ids[s][pos[s]]], s});
+        }
+        while (!heap.empty()) {
+            const Head h = heap.top();
+            heap.pop();
+            if (h.id > 0xFFFFFFFFULL) return set_error(COBS_ERR_ARG, "document id beyond 32 bits");
+            ids_out[k] = (uint32_t)h.id;
+            scores_out[k] = h.score;
+            k++;
+            const uint64_t p = ++pos[h.shard];
+            if (p < end[h.shard]) heap.push(Head{scores[h.shard][p], global_ids[h.shard][ids[h.shard][p]], h.shard});
+        }
+        hit_offsets_out[q + 1] = k;
     }
-    *n_out = k;
     return COBS_OK;
 }

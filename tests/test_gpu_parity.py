@@ -359,16 +359,23 @@ def _autotune_and_check(wl, ref, dix):
     cfg = eng.autotune(dq, do, wl.q_off, dt)
     widths = (32, 64, 128, 256) if wl.num_hashes == 1 else (32, 64, 128)
     assert cfg["slice_bytes"] in widths and cfg["ctas_per_sm"] >= 1 and cfg["l2_hints"] in (1, 2, 3, 4)
+    assert (cfg["split"], cfg["split_part"]) in ((0, 0), (1, 0), (2, 4080), (2, 1024))
+    assert cfg["class_streams"] in (0, 2)
     st = eng.stats()
     assert (st["slice_bytes"], st["ctas_per_sm"]) == (cfg["slice_bytes"], cfg["ctas_per_sm"])
     for flags in (cobs.COBS_BATCHED, cobs.COBS_GRAPH):
         got = eng.query_host(wl.queries, wl.q_off, wl.thresholds, flags)
         assert_results_equal(got, ref, wl.query_list(), wl.thresholds)
+    # a second engine on the same index and batch shape takes the cached choice
+    again = cobs.Engine(dix).autotune(dq, do, wl.q_off, dt)
+    assert again.pop("from_cache")
+    cfg.pop("from_cache")
+    assert again == cfg
 
 
 def test_autotune_single_hash(compact):
-    # the sweep (slice width x CTAs per SM x L2 hints) ends on one of its shapes
-    # and the engine's results stay those of the oracle
+    # the sweep (slice width, CTAs per SM, L2 hints, term chunk, class streams)
+    # ends on one of its shapes and the engine's results stay those of the oracle
     wl, ref, dix = compact
     _autotune_and_check(wl, ref, dix)
 
