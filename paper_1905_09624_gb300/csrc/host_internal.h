@@ -12,6 +12,22 @@
 #include "kernels.cuh"
 #include "status.h"
 
+// Return a status from a CUDA call that failed (OOM for an allocation) or from a
+// library call that failed, with the message recorded.
+#define CU(call)                                                                                        \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return set_error(e_ == cudaErrorMemoryAllocation ? COBS_ERR_OOM : COBS_ERR_CUDA, "%s: %s", \
+                             #call, cudaGetErrorString(e_));                                            \
+    } while (0)
+
+#define TRY(expr)                         \
+    do {                                  \
+        cobs_status s_ = (expr);          \
+        if (s_ != COBS_OK) return s_;     \
+    } while (0)
+
 namespace cobs {
 
 // NVTX range over a host scope: shows planning, enqueueing and waiting on a
@@ -106,6 +122,10 @@ struct ResultStore;
 // Barrett constant floor(2^64 / w) of a Bloom size w (UINT64_MAX for w <= 1),
 // the per-block modulus constant of barrett_mod.
 uint64_t barrett_m_of(uint64_t w);
+
+// The engine's table of row slices of lpq 16-byte lanes (made anew when the
+// width changes).
+cobs_status ensure_slices(cobs_engine *eng, uint32_t lpq);
 
 }  // namespace cobs
 
