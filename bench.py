@@ -66,7 +66,7 @@ def run_config(wl, name, world):
                 parallelism=f"replicas x{world}" if world > 1 else "1 GPU")
 
 
-def l2_read_peak(cobs, torch, stream, nbytes=64 << 20, reps=150, trials=5):
+def l2_read_peak(cobs, torch, stream, nbytes=64 << 20, reps=150, trials=5, ctas_per_sm=0):
     """Read bandwidth of the L2 cache measured here: cobs_probe_l2_read over a
     buffer well inside L2 (16-byte loads that bypass L1, a full grid), best of
     `trials` launches after a warming one, CUDA events on the launching stream."""
@@ -77,7 +77,7 @@ def l2_read_peak(cobs, torch, stream, nbytes=64 << 20, reps=150, trials=5):
     for t in range(trials + 1):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        cobs.probe_l2_read(buf.data_ptr(), nbytes, reps, sink.data_ptr(), 0, stream.cuda_stream)
+        cobs.probe_l2_read(buf.data_ptr(), nbytes, reps, sink.data_ptr(), ctas_per_sm, stream.cuda_stream)
         e1.record(stream)
         e1.synchronize()
         if t:
@@ -210,6 +210,23 @@ def oracle_baseline(wl, sample_queries, budget_s=20.0, nthreads=None):
                 "seconds": t, "terms": terms,
                 "all_cores": {"value": terms / t_all if t_all else None, "cores": ncores, "seconds": t_all,
                               "sample": "the same queries, one thread per host core"}}
+
+
+def run_l2_sweep(args):
+    """--l2-sweep: the L2 read probe over buffer sizes and passes per launch
+    (one JSON line per point); the bench's own ceiling is l2_read_peak."""
+    import torch
+    from paper_1905_09624_gb300 import cobs
+    if not torch.cuda.is_available():
+        raise SystemExit("--l2-sweep needs a CUDA GPU")
+    stream = torch.cuda.Stream()
+    for mb in (8, 16, 32, 48, 64, 96, 256, 1024):
+        for reps in (10, 40):
+            for cps in (0, 4):
+                gbs = l2_read_peak(cobs, torch, stream, nbytes=mb << 20, reps=reps, trials=5, ctas_per_sm=cps)
+                print(json.dumps({"buffer_mb": mb, "reps": reps, "ctas_per_sm": cps or 8, "gbs": gbs}), flush=True)
+    print(json.dumps({"bench_l2_read_peak_gbs": l2_read_peak(cobs, torch, stream)}), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -743,6 +760,29 @@ def run_gpu(args):
         plain = {"value": pr[0]["terms"] / pt, "unit": UNIT, "ms": pt * 1e3,
                  "row_gbs_logical": pr[0]["row_bytes"] / pt / 1e9,
                  "launches": pr[0]["launches"], "results_identical_to_batched": bool(same)}
+    # ---- hit emission under many hits: the first 1,000 queries at K = 1 permille
+    # (min score 1: nearly every document is a hit) against the same queries at
+    # the workload's thresholds, batched form, gather and hit phases
+    low_k = None
+    if not args.skip_low_k:
+        m = min(1000, wl.n_queries)
+        qo = wl.q_off[:m + 1].copy()
+        sq = torch.from_numpy(wl.queries[:int(qo[-1])]).to("cuda")
+        so = torch.from_numpy(qo.view(np.int64)).to("cuda")
+        low_k = {"queries": m}
+        for label, thr_host in (("workload_thresholds", wl.thresholds[:m].copy()),
+                                ("k_1_permille", np.ones(m, np.uint16))):
+            st_thr = torch.from_numpy(thr_host.view(np.int16)).to("cuda")
+            torch.cuda.synchronize()
+            runs = []
+            for rep in range(4):
+                flush_l2()
+                eng.query_device(sq, so, qo, st_thr, cobs.COBS_BATCHED)
+                runs.append(eng.stats())
+            hits = int(eng.download_arrays()[2][-1])
+            best = min(runs[1:], key=lambda r: r["ms_gather"])
+            low_k[label] = {"ms_gather": best["ms_gather"], "ms_hits": best["ms_hits"], "hits": hits}
+        del sq, so, st_thr
     # ---- the same batch on a streamed copy of the index: rows in pinned host
     # memory, copied block by block into a ring of device slots every step
     streamed = None
@@ -773,6 +813,7 @@ def run_gpu(args):
         streamed = {"value": s_terms / args.streamed_steps / (sm / 1e3), "unit": UNIT, "ms_per_step": sm,
                     "steps": args.streamed_steps, "h2d_index_bytes_per_step": sst["h2d_index_bytes"],
                     "h2d_index_gbs": sst["h2d_index_bytes"] / (sm / 1e3) / 1e9, "stage_slots": n_slots,
+                    "rows_host_numa_node": sst["stream_numa_node"],
                     "stage_bytes": n_slots * slot, "index_bytes": info["rows_bytes"],
                     "results_identical_to_resident": bool(same)}
         del seng, sdix
@@ -891,7 +932,7 @@ def run_gpu(args):
                      "gbs_with_h2d": int(wl.doc_off[-1]) / build_h2d_s / 1e9,
                      "index_bytes": info["rows_bytes"], "blocks": len(info["blocks"])},
            "speedup_batched_over_plain": (value / plain["value"]) if plain else None,
-           "streamed": streamed, "multi_index": multi, "insert": insert}
+           "streamed": streamed, "multi_index": multi, "insert": insert, "many_hits": low_k}
     if plain:
         out["plain"]["frac_of_hbm_peak"] = plain["row_gbs_logical"] / peak
 
@@ -941,6 +982,7 @@ def main():
     ap.add_argument("--streamed-steps", type=int, default=10, help="timed steps of the streamed and multi-index runs")
     ap.add_argument("--skip-multi", action="store_true", help="skip the multi-index measurement")
     ap.add_argument("--skip-insert", action="store_true", help="skip the incremental-insertion measurement")
+    ap.add_argument("--skip-low-k", action="store_true", help="skip the K = 1 permille hit-emission measurement")
     ap.add_argument("--gather-feed", type=int, default=0, help="0 default, 1 cp.async ring, 2 TMA gather")
     ap.add_argument("--l2-hints", type=int, default=0, help="L2 eviction hints of the gather (0 default, 1..4)")
     ap.add_argument("--workloads", default=None,
@@ -959,6 +1001,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=1.5)
     ap.add_argument("--serve-inflight", type=int, default=3, help="waves on the device at once")
     ap.add_argument("--serve-wave-max", type=int, default=4096, help="queries per wave at most")
+    ap.add_argument("--l2-sweep", action="store_true", help="print the L2 read probe over buffer sizes and exit")
     ap.add_argument("--shard", action="store_true",
                     help="document-block sharding over the ranks instead of replicas (strong scaling)")
     ap.add_argument("--configs", default="cfg1,cfg4,cfg3",
@@ -973,6 +1016,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.l2_sweep:
+        return run_l2_sweep(args)
     if args.shard:
         return run_gpu_sharded(args)
     return run_gpu(args)

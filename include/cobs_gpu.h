@@ -350,7 +350,8 @@ typedef struct cobs_query_stats {
     double ms_host;           /* host time of the last query call: planning and enqueueing */
     uint64_t h2d_index_bytes; /* streamed index: row bytes copied to the staging ring */
     uint32_t split_part;      /* terms per part of the split queries (0: none split) */
-    uint32_t _pad2;
+    int32_t stream_numa_node; /* streamed index: host NUMA node its rows are bound to (the one
+                                 nearest the device); -1 = none (no NUMA, or not streamed) */
 } cobs_query_stats;
 cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out);
 

@@ -73,7 +73,8 @@ class cobs_query_stats(ctypes.Structure):
                 ("n_tiles", ctypes.c_uint64), ("gather_launches", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("slice_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("l2_hints", ctypes.c_uint32),
                 ("split_queries", ctypes.c_uint32), ("ms_host", ctypes.c_double),
-                ("h2d_index_bytes", ctypes.c_uint64), ("split_part", ctypes.c_uint32), ("_pad2", ctypes.c_uint32)]
+                ("h2d_index_bytes", ctypes.c_uint64), ("split_part", ctypes.c_uint32),
+                ("stream_numa_node", ctypes.c_int32)]
 
 
 class cobs_serve_cfg(ctypes.Structure):

@@ -1057,5 +1057,6 @@ extern "C" cobs_status cobs_engine_stats(cobs_engine *eng, cobs_query_stats *out
     out->ms_host = eng->stat_host_ms;
     out->h2d_index_bytes = eng->stat_h2d_index_bytes;
     out->split_part = eng->bp.part_terms;
+    out->stream_numa_node = eng->dix->streamed ? eng->dix->host_rows.node : -1;
     return COBS_OK;
 }

@@ -66,19 +66,20 @@ struct DevBuf {
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
-// Pinned host allocation that only grows.
+// Pinned host allocation that only grows.  ensure() takes it from the CUDA
+// allocator; ensure_on_node() maps pages bound to one host NUMA node and pins
+// them (the node nearest a device, so its copies cross no socket link).
 struct PinBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    size_t mapped = 0;  // ensure_on_node: bytes of the mapping (0: from cudaMallocHost)
+    int node = -1;      // ensure_on_node: the NUMA node the pages are bound to
     PinBuf() = default;
     PinBuf(const PinBuf &) = delete;
     PinBuf &operator=(const PinBuf &) = delete;
     ~PinBuf() { release(); }
-    void release() {
-        if (p) cudaFreeHost(p);
-        p = nullptr;
-        bytes = 0;
-    }
+    void release();
+    cudaError_t ensure_on_node(size_t n, int numa_node);
     cudaError_t ensure(size_t n) {
         if (n == 0) n = 16;
         if (n <= bytes) return cudaSuccess;
@@ -148,7 +149,7 @@ struct cobs_device_index {
     cobs::DevBuf rows, dblocks, dperm, pgroups;
     // streamed index: rows in pinned host memory, copied block by block per batch
     bool streamed = false;
-    cobs::PinBuf host_rows;
+    cobs::PinBuf host_rows;            // on the device's nearest host NUMA node where the system reports one
     uint64_t max_block_bytes = 0;
     // multi-index view: rows borrowed from resident parts; block b's rows start at
     // rows_view + dev_row_offset[b] on the device (blocks[].row_offset stays the

@@ -596,7 +596,12 @@ static cobs_status load_impl(const cobs_index *ix, int device, void *stream, boo
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
     if (streamed) {
-        e = dix->host_rows.ensure(dix->rows_bytes);
+        int numa = -1;  // the host node nearest the device, if the system has NUMA
+        if (cudaDeviceGetAttribute(&numa, cudaDevAttrHostNumaId, device) != cudaSuccess) {
+            numa = -1;
+            cudaGetLastError();
+        }
+        e = dix->host_rows.ensure_on_node(dix->rows_bytes, numa);
         if (e == cudaSuccess && dix->rows_bytes) memcpy(dix->host_rows.p, ix->rows.data(), dix->rows_bytes);
     } else {
         e = dix->rows.ensure(dix->rows_bytes);
