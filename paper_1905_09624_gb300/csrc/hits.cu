@@ -11,33 +11,50 @@ constexpr uint32_t SORT_THREADS = 128;
 constexpr uint32_t SORT_SMEM_KEYS = 1024;
 
 // Exclusive scan of the per-query hit counts (one CTA), threshold per query,
-// reset of the scatter cursors.
+// reset of the scatter cursors.  The CTA walks the queries in tiles of
+// SCAN_THREADS, one query per thread (coalesced), scans each tile by warp
+// shuffles and the warps' sums, and carries the running total to the next tile.
 __global__ void __launch_bounds__(SCAN_THREADS) k_hits_scan(HitsArgs a) {
-    __shared__ unsigned long long s_part[SCAN_THREADS];
+    constexpr uint32_t NW = SCAN_THREADS / 32;
+    __shared__ unsigned long long s_warp[NW];
+    __shared__ unsigned long long s_carry;
     const uint32_t n = a.n_queries;
-    const uint32_t per = (n + SCAN_THREADS - 1) / SCAN_THREADS;
-    const uint32_t q0 = threadIdx.x * per;
-    const uint32_t q1 = q0 + per < n ? q0 + per : n;
-    unsigned long long sum = 0;
-    for (uint32_t q = q0; q < q1; q++) sum += a.qcount[q];
-    s_part[threadIdx.x] = sum;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    for (uint32_t t0 = 0; t0 < n; t0 += SCAN_THREADS) {
+        const uint32_t q = t0 + threadIdx.x;
+        const uint32_t c = q < n ? a.qcount[q] : 0u;
+        unsigned long long incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, d);
+            if ((int)lane >= d) incl += y;
+        }
+        if (lane == 31u) s_warp[warp] = incl;
+        __syncthreads();  // warp sums written; s_carry of the previous tile final
+        if (warp == 0) {
+            unsigned long long w = lane < NW ? s_warp[lane] : 0ULL;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, w, d);
+                if ((int)lane >= d) w += y;
+            }
+            if (lane < NW) s_warp[lane] = w;  // inclusive sums of the warps
+        }
+        __syncthreads();
+        const unsigned long long tile_total = s_warp[NW - 1];
+        const unsigned long long before = s_carry + (warp ? s_warp[warp - 1] : 0ULL);
+        if (q < n) {
+            a.hit_off[q] = before + incl - c;
+            if (c > SORT_SMEM_KEYS) a.big_list[atomicAdd(a.big_count, 1ULL)] = q;
+            a.qcursor[q] = 0;
+            a.min_score[q] = (uint32_t)(((uint64_t)a.thr[q] * a.ell[q] + 999u) / 1000u);
+        }
+        __syncthreads();  // every thread read s_carry and s_warp
+        if (threadIdx.x == 0) s_carry += tile_total;
+    }
     __syncthreads();
-    for (uint32_t d = 1; d < SCAN_THREADS; d <<= 1) {
-        unsigned long long v = threadIdx.x >= d ? s_part[threadIdx.x - d] : 0ULL;
-        __syncthreads();
-        s_part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    unsigned long long run = s_part[threadIdx.x] - sum;
-    for (uint32_t q = q0; q < q1; q++) {
-        a.hit_off[q] = run;
-        if (a.qcount[q] > SORT_SMEM_KEYS) a.big_list[atomicAdd(a.big_count, 1ULL)] = q;
-        run += a.qcount[q];
-        a.qcursor[q] = 0;
-        uint32_t ell = a.ell[q];
-        a.min_score[q] = (uint32_t)(((uint64_t)a.thr[q] * ell + 999u) / 1000u);
-    }
-    if (threadIdx.x == SCAN_THREADS - 1) a.hit_off[n] = s_part[SCAN_THREADS - 1];
+    if (threadIdx.x == 0) a.hit_off[n] = s_carry;
 }
 
 __global__ void k_hits_scatter(HitsArgs a) {

@@ -12,7 +12,10 @@ namespace {
 // only (ld.global.cg: no L1 allocation), folding them into one word so the loads
 // stay live; the grid strides over the buffer `reps` times.
 constexpr int PROBE_THREADS = 256;
-constexpr int PROBE_UNROLL = 8;
+#ifndef COBS_PROBE_UNROLL
+#define COBS_PROBE_UNROLL 8
+#endif
+constexpr int PROBE_UNROLL = COBS_PROBE_UNROLL;  // loads in flight per thread
 
 // a volatile L2 load: every pass really reads the buffer again
 __device__ __forceinline__ uint4 ld_cg_volatile(const uint4 *p) {
