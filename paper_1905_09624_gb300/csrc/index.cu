@@ -19,6 +19,10 @@
 
 using namespace cobs;
 
+#ifndef COBS_COUNT_WAVE_MB
+#define COBS_COUNT_WAVE_MB 2048  // partition bytes of one wave of the distinct count, MB
+#endif
+
 extern "C" const char *cobs_version(void) { return "cobs_gpu 0.1 (sm_103a)"; }
 extern "C" uint32_t cobs_abi_version(void) { return COBS_GPU_ABI_VERSION; }
 
@@ -210,7 +214,9 @@ static cobs_status count_partitioned(const cobs_params *P, const uint8_t *d_docs
     std::vector<uint64_t> chunk_p0;
     size_t free_b = 0, total_b = 0;
     CU(cudaMemGetInfo(&free_b, &total_b));
-    uint64_t budget = std::min<uint64_t>(free_b / 4, 2ULL << 30);  // bytes of partitions per wave
+    // bytes of partitions per wave: fewer, larger waves cost fewer launches,
+    // memsets and tails (a quarter of the free memory at most)
+    uint64_t budget = std::min<uint64_t>(free_b / 4, (uint64_t)COBS_COUNT_WAVE_MB << 20);
     if (build_scratch_override()) budget = build_scratch_override();
     struct Wave { uint64_t c0, c1, q0, q1, slots; };  // chunks [c0, c1), partitions [q0, q1), term slots
     std::vector<Wave> waves;
