@@ -17,13 +17,25 @@ struct ChunkStage {
     uint16_t inv[(W + 32) / 16 + 3];
 };
 
-// Stage the windows [p0, p0 + nwin) of one document.  Cooperative; ends with a
-// barrier.
-template <uint32_t W>
+// Stage the windows [p0, p0 + nwin) of one document.  Cooperative (NT threads);
+// every thread issues all of its byte loads before it stores any, so they are
+// in flight together; ends with a barrier.
+template <uint32_t NT, uint32_t W>
 __device__ __forceinline__ void stage_chunk(ChunkStage<W> &st, const uint8_t *doc, uint64_t p0, uint32_t nwin,
                                             uint32_t k, bool dna) {
+    constexpr uint32_t PER = (W + 32 + NT - 1) / NT;
     const uint32_t nbytes = nwin + k - 1;
-    for (uint32_t i = threadIdx.x; i < nbytes; i += blockDim.x) st.bytes[i] = doc[p0 + i];
+    uint8_t v[PER];
+#pragma unroll
+    for (uint32_t j = 0; j < PER; j++) {
+        const uint32_t i = threadIdx.x + j * NT;
+        v[j] = i < nbytes ? doc[p0 + i] : (uint8_t)0;
+    }
+#pragma unroll
+    for (uint32_t j = 0; j < PER; j++) {
+        const uint32_t i = threadIdx.x + j * NT;
+        if (i < nbytes) st.bytes[i] = v[j];
+    }
     __syncthreads();
     if (dna) {
         pack_bases(st.bytes, nbytes, st.pk, st.inv);
@@ -50,7 +62,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_doc_count(CountArgs a) {
     const uint64_t npos = len >= a.k ? len - a.k + 1 : 0;
     const uint64_t p0 = a.chunk_p0[blockIdx.x];
     const uint32_t nwin = (uint32_t)(npos - p0 < COUNT_CHUNK ? npos - p0 : COUNT_CHUNK);
-    stage_chunk(st, a.docs + a.doc_off[d], p0, nwin, a.k, a.kind != KIND_BYTES);
+    stage_chunk<BUILD_THREADS>(st, a.docs + a.doc_off[d], p0, nwin, a.k, a.kind != KIND_BYTES);
     unsigned long long *table = a.tables + a.table_base[d];
     const uint32_t cap = a.table_cap[d];
     const uint64_t mask = kmer_mask(a.k);
@@ -75,7 +87,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_doc_setbits(SetBitsArgs a) {
     const uint64_t npos = len >= a.k ? len - a.k + 1 : 0;
     const uint64_t p0 = a.chunk_p0[blockIdx.x];
     const uint32_t nwin = (uint32_t)(npos - p0 < SETBITS_CHUNK ? npos - p0 : SETBITS_CHUNK);
-    stage_chunk(st, a.docs + a.doc_off[d], p0, nwin, a.k, a.kind != KIND_BYTES);
+    stage_chunk<BUILD_THREADS>(st, a.docs + a.doc_off[d], p0, nwin, a.k, a.kind != KIND_BYTES);
     const DevBlock blk = a.blocks[a.doc_block[d]];
     const uint32_t j = a.doc_col[d];
     const uint32_t bit = 1u << (j & 31u);
@@ -95,16 +107,17 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_doc_setbits(SetBitsArgs a) {
 // ------------------------------------------------ partitioned distinct count
 // Scatter: the CTA's windows get their partition (multiply-shift of the high 32
 // bits of mix64 of the term) and a rank within it from shared-memory counters; one
-// global atomic per partition reserves the CTA's run, then every term is written
-// to its slot.  Slots past the partition's capacity are not written: the count
-// pass sees the overflow and the document is recounted with a global set.
+// global atomic per partition reserves the CTA's run, then every term -- taken
+// again from the staged bases -- is written to its slot.  Slots past the
+// partition's capacity are not written: the count pass sees the overflow and the
+// document is recounted with a global set.  Shared memory: the stage, a word per
+// window and two counters per partition (max_parts), so several CTAs fit an SM.
 __global__ void __launch_bounds__(PART_THREADS) k_part_scatter(PartArgs a) {
     __shared__ ChunkStage<COUNT_CHUNK> st;
     extern __shared__ __align__(16) unsigned char s_dyn[];
-    unsigned long long *s_code = reinterpret_cast<unsigned long long *>(s_dyn);  // COUNT_CHUNK
-    uint32_t *s_pr = reinterpret_cast<uint32_t *>(s_code + COUNT_CHUNK);          // partition << 12 | rank
-    uint32_t *s_hist = s_pr + COUNT_CHUNK;                                         // PART_MAX
-    uint32_t *s_base = s_hist + PART_MAX;                                          // PART_MAX
+    uint32_t *s_pr = reinterpret_cast<uint32_t *>(s_dyn);  // COUNT_CHUNK: partition << 12 | rank
+    uint32_t *s_hist = s_pr + COUNT_CHUNK;                  // max_parts
+    uint32_t *s_base = s_hist + a.max_parts;                // max_parts
     const uint32_t d = a.chunk_doc[blockIdx.x];
     const uint64_t len = a.doc_off[d + 1] - a.doc_off[d];
     const uint64_t npos = len >= a.k ? len - a.k + 1 : 0;
@@ -112,7 +125,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_part_scatter(PartArgs a) {
     const uint32_t nwin = (uint32_t)(npos - p0 < COUNT_CHUNK ? npos - p0 : COUNT_CHUNK);
     const uint32_t P = a.n_parts[d];
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) s_hist[i] = 0u;
-    stage_chunk(st, a.docs + a.doc_off[d], p0, nwin, a.k, a.kind != KIND_BYTES);  // barriers order the zeroing
+    stage_chunk<PART_THREADS>(st, a.docs + a.doc_off[d], p0, nwin, a.k, a.kind != KIND_BYTES);  // barriers order the zeroing
     const uint64_t mask = kmer_mask(a.k);
     for (uint32_t w = threadIdx.x; w < nwin; w += blockDim.x) {
         uint64_t code;
@@ -124,7 +137,6 @@ __global__ void __launch_bounds__(PART_THREADS) k_part_scatter(PartArgs a) {
                 const uint64_t h = mix64(code);
                 const uint32_t part = (uint32_t)(((h >> 32) * (uint64_t)P) >> 32);
                 pr = (part << 12) | atomicAdd(&s_hist[part], 1u);
-                s_code[w] = code;
             }
         }
         s_pr[w] = pr;
@@ -141,7 +153,9 @@ __global__ void __launch_bounds__(PART_THREADS) k_part_scatter(PartArgs a) {
         if (pr == 0xFFFFFFFFu) continue;
         const uint32_t part = pr >> 12;
         const uint32_t slot = s_base[part] + (pr & 4095u);
-        if (slot < cap) out[(uint64_t)part * cap + slot] = s_code[w];
+        uint64_t code = 0;
+        chunk_term(st, w, a.kind, a.k, mask, &code);  // a term: pr was set for it
+        if (slot < cap) out[(uint64_t)part * cap + slot] = code;
     }
 }
 
@@ -191,9 +205,10 @@ __global__ void __launch_bounds__(PART_THREADS) k_part_count(PartArgs a) {
 }
 
 void launch_part_scatter(const PartArgs &a, uint32_t n_chunks, cudaStream_t s) {
-    constexpr int dyn = (int)(COUNT_CHUNK * 8 + COUNT_CHUNK * 4 + 2 * PART_MAX * 4);
+    constexpr int most = (int)(COUNT_CHUNK * 4 + 2 * PART_MAX * 4);
     static PerDeviceOnce once;
-    once([] { cudaFuncSetAttribute(k_part_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn); });
+    once([] { cudaFuncSetAttribute(k_part_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, most); });
+    const size_t dyn = (size_t)COUNT_CHUNK * 4 + 2 * (size_t)a.max_parts * 4;
     if (n_chunks) k_part_scatter<<<n_chunks, PART_THREADS, dyn, s>>>(a);
 }
 
@@ -223,7 +238,7 @@ __global__ void __launch_bounds__(FILTER_THREADS) k_doc_filter(FilterArgs a) {
     // the bytes of the next tile are loaded into registers while this tile's
     // windows are processed (PRE bytes per thread), then staged
     constexpr uint32_t PRE = (FILTER_TILE + 32 + FILTER_THREADS - 1) / FILTER_THREADS;
-    if (npos) stage_chunk(st, doc, 0, (uint32_t)(npos < FILTER_TILE ? npos : FILTER_TILE), a.k, dna);
+    if (npos) stage_chunk<FILTER_THREADS>(st, doc, 0, (uint32_t)(npos < FILTER_TILE ? npos : FILTER_TILE), a.k, dna);
     for (uint64_t p0 = 0; p0 < npos; p0 += FILTER_TILE) {
         const uint32_t nwin = (uint32_t)(npos - p0 < FILTER_TILE ? npos - p0 : FILTER_TILE);
         const uint64_t q0 = p0 + FILTER_TILE;

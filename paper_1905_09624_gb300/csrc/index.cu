@@ -218,9 +218,9 @@ static cobs_status count_partitioned(const cobs_params *P, const uint8_t *d_docs
     // memsets and tails (a quarter of the free memory at most)
     uint64_t budget = std::min<uint64_t>(free_b / 4, (uint64_t)COBS_COUNT_WAVE_MB << 20);
     if (build_scratch_override()) budget = build_scratch_override();
-    struct Wave { uint64_t c0, c1, q0, q1, slots; };  // chunks [c0, c1), partitions [q0, q1), term slots
+    struct Wave { uint64_t c0, c1, q0, q1, slots, max_parts; };  // chunks [c0, c1), partitions [q0, q1), term slots
     std::vector<Wave> waves;
-    Wave wv{0, 0, 0, 0, 0};
+    Wave wv{0, 0, 0, 0, 0, 1};
     for (uint32_t d : docs) {
         const uint64_t np = npos[d];
         const uint64_t pd = std::max<uint64_t>(1, (np + PART_WINDOWS - 1) / PART_WINDOWS);
@@ -230,8 +230,9 @@ static cobs_status count_partitioned(const cobs_params *P, const uint8_t *d_docs
         const uint64_t need = pd * cap;
         if (wv.q1 > wv.q0 && (wv.slots + need) * 8 > budget) {
             waves.push_back(wv);
-            wv = Wave{wv.c1, wv.c1, wv.q1, wv.q1, 0};
+            wv = Wave{wv.c1, wv.c1, wv.q1, wv.q1, 0, 1};
         }
+        wv.max_parts = std::max<uint64_t>(wv.max_parts, pd);
         n_parts[d] = (uint32_t)pd;
         part_cap[d] = (uint32_t)cap;
         part0[d] = wv.q1 - wv.q0;
@@ -300,6 +301,7 @@ static cobs_status count_partitioned(const cobs_params *P, const uint8_t *d_docs
         pa.overflow = dover.as<uint32_t>();
         pa.kind = P->term_kind;
         pa.k = P->q;
+        pa.max_parts = (uint32_t)w.max_parts;
         launch_part_scatter(pa, (uint32_t)(w.c1 - w.c0), s);
         launch_part_count(pa, (uint32_t)(w.q1 - w.q0), s);
         CU(cudaGetLastError());

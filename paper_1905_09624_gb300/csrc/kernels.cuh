@@ -261,6 +261,7 @@ struct PartArgs {
     uint32_t *has_empty;           // per document flag for the EMPTY code (bytes kind)
     uint32_t *overflow;            // per document: a partition overflowed
     uint32_t kind, k;
+    uint32_t max_parts;            // scatter: the largest P_d of the launch's documents
 };
 void launch_part_scatter(const PartArgs &a, uint32_t n_chunks, cudaStream_t s);
 void launch_part_count(const PartArgs &a, uint32_t n_parts, cudaStream_t s);
