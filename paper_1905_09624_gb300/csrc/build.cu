@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_part_scatter(PartArgs a) {
 // Count: the distinct terms of one partition in a shared-memory open-addressing
 // set (home slot from the low 32 bits of the hash: the high bits chose the
 // partition), added to the document's count once per warp.
-__global__ void __launch_bounds__(PART_THREADS) k_part_count(PartArgs a) {
+__global__ void __launch_bounds__(PART_COUNT_THREADS) k_part_count(PartArgs a) {
     extern __shared__ __align__(16) unsigned long long s_set[];  // PART_SET_SLOTS
     const uint32_t d = a.part_doc[blockIdx.x];
     const uint32_t n = a.part_count[blockIdx.x];
@@ -216,7 +216,7 @@ void launch_part_count(const PartArgs &a, uint32_t n_parts, cudaStream_t s) {
     constexpr int dyn = (int)(PART_SET_SLOTS * 8);
     static PerDeviceOnce once;
     once([] { cudaFuncSetAttribute(k_part_count, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn); });
-    if (n_parts) k_part_count<<<n_parts, PART_THREADS, dyn, s>>>(a);
+    if (n_parts) k_part_count<<<n_parts, PART_COUNT_THREADS, dyn, s>>>(a);
 }
 
 // ------------------------------------------------- per-document filters

@@ -244,6 +244,10 @@ constexpr uint32_t PART_SET_SLOTS = COBS_PART_SET_SLOTS;  // shared-memory set o
 constexpr uint32_t PART_WINDOWS = PART_SET_SLOTS * 3 / 8;  // windows per partition (target): load <= 0.44
 constexpr uint32_t PART_MAX = 2048;                        // partitions of a document
 constexpr uint32_t PART_THREADS = 256;
+#ifndef COBS_PART_COUNT_THREADS
+#define COBS_PART_COUNT_THREADS 512
+#endif
+constexpr uint32_t PART_COUNT_THREADS = COBS_PART_COUNT_THREADS;  // threads of a partition's count CTA
 struct PartArgs {
     const uint8_t *docs;
     const uint64_t *doc_off;
