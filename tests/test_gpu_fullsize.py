@@ -41,6 +41,10 @@ def test_cfg2_full_size_index_and_sampled_queries():
         eng.query_device(d_q, d_off, wl.q_off, d_thr, cobs.COBS_GRAPH)
         graph = eng.download_arrays()
         assert all(np.array_equal(a, b) for a, b in zip(graph, batched))
+    # so does the plain form, one query per launch, on the whole batch
+    eng.query_device(d_q, d_off, wl.q_off, d_thr, cobs.COBS_PLAIN)
+    plain = eng.download_arrays()
+    assert all(np.array_equal(a, b) for a, b in zip(plain, batched))
     # and so does the pipelined host path of the end-to-end measurement
     pin = torch.empty(len(wl.queries), dtype=torch.uint8, pin_memory=True).numpy()
     pin[:] = wl.queries
@@ -72,6 +76,24 @@ def _graph_form_results(dix, wl):
     return res
 
 
+def _plain_matches(dix, wl, res, m):
+    """The plain form (one query per launch) on the first m queries, as a batch
+    of its own, gives exactly the hits of the full batch's first m queries."""
+    import torch
+    qo = wl.q_off[:m + 1].copy()
+    d_q = torch.from_numpy(wl.queries[:int(qo[-1])].copy()).cuda()
+    d_off = torch.from_numpy(qo.view(np.int64)).cuda()
+    d_thr = torch.from_numpy(wl.thresholds[:m].copy().view(np.int16)).cuda()
+    eng = cobs.Engine(dix)
+    torch.cuda.synchronize()
+    eng.query_device(d_q, d_off, qo, d_thr, cobs.COBS_PLAIN)
+    plain = eng.download_arrays()
+    for i in range(m):
+        assert _query(plain, i)[:2] == _query(res, i)[:2], i
+        a, b = _query(plain, i), _query(res, i)
+        assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3]), i
+
+
 def _query(res, i):
     h0, h1 = int(res[2][i]), int(res[2][i + 1])
     return int(res[0][i]), int(res[1][i]), res[3][h0:h1], res[4][h0:h1]
@@ -95,6 +117,7 @@ def test_cfg4_full_size_index_and_sampled_queries():
     assert len(ref.blocks()) == 13
     assert_index_equal(dix, ref)
     res = _graph_form_results(dix, wl)
+    _plain_matches(dix, wl, res, 2000)  # the fused plain kernel, h = 3, 13 blocks
     ql = wl.query_list()
     sample = _sample_with_longest(wl, 300, 20, 4004)
     from concurrent.futures import ThreadPoolExecutor
@@ -137,6 +160,9 @@ def test_cfg3_full_size_plan_sampled_blocks_and_queries():
         assert np.array_equal(got_rows[lo:hi], want_rows[lo:hi]), f"block {b} differs"
     del host, info, got_rows
     res = _graph_form_results(dix, wl)
+    # the plain form on 500 queries: most are longer than one term round (terms
+    # kernels, then the gather kernel), the others run fused
+    _plain_matches(dix, wl, res, 500)
     perm = ref.perm()
     in_picked = np.zeros(wl.n_docs, dtype=bool)
     for b in picked:
