@@ -490,6 +490,7 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
     ta.kind = P.term_kind;
     ta.k = P.q;
     ta.smem_slots = bp.smem_slots;
+    ta.smem_table = terms_smem_table(bp.smem_slots);
 
     if (flags & COBS_PLAIN) {
         // One query per launch over (column group x term chunk) tiles, which

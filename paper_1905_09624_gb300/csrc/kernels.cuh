@@ -35,7 +35,28 @@ constexpr uint32_t TERMS_THREADS = COBS_TERMS_THREADS;
 constexpr uint32_t TERMS_SEG = 8;             // windows rolled by one thread per round
 constexpr uint32_t TERMS_BUCKET_BITS = 6;     // terms are emitted in 64 row buckets per block
 constexpr uint32_t TERMS_BUCKETS = 1u << TERMS_BUCKET_BITS;
-constexpr uint32_t TERMS_BLOCKS_PER_PASS = 4;   // blocks whose rows one pass over the terms computes
+#ifndef COBS_TERMS_BP
+#define COBS_TERMS_BP 4
+#endif
+constexpr uint32_t TERMS_BLOCKS_PER_PASS = COBS_TERMS_BP;  // blocks whose rows one pass over the terms computes
+// An on-chip set of a short query takes up to TERMS_SET_SPREAD slots per window
+// (at least 2, the size every set is correct with): a sparser table means fewer
+// probes and less divergence among a warp's insertions.  The launch gives the
+// table region as much of a shared-memory budget of TERMS_SMEM_BUDGET bytes per
+// CTA (set and list) as the spread can use.
+constexpr uint32_t TERMS_SET_SPREAD = 4;
+#ifndef COBS_TERMS_SMEM_BUDGET
+#define COBS_TERMS_SMEM_BUDGET 40960
+#endif
+constexpr uint32_t TERMS_SMEM_BUDGET = COBS_TERMS_SMEM_BUDGET;
+// table slots of the on-chip region for a launch whose largest on-chip set has
+// `slots` = set_slots(windows) slots (its list holds slots / 2 terms)
+inline uint32_t terms_smem_table(uint32_t slots) {
+    const uint32_t budget = TERMS_SMEM_BUDGET / 8 > slots / 2 ? TERMS_SMEM_BUDGET / 8 - slots / 2 : 0u;
+    const uint32_t spread = slots / 2 * TERMS_SET_SPREAD;
+    const uint32_t t = budget < spread ? budget : spread;
+    return t > slots ? t : slots;
+}
 
 struct TermsArgs {
     const uint8_t *bytes;          // queries concatenated
@@ -51,6 +72,8 @@ struct TermsArgs {
     uint32_t n_blocks, h, kind, k;
     uint32_t q0;                   // first query handled by blockIdx.x == 0
     uint32_t smem_slots;           // sets of up to this many slots (<= TERMS_SMEM_SLOTS) and their lists live in shared memory
+    uint32_t smem_table;           // slots of the on-chip table region (>= smem_slots; 0: smem_slots); an on-chip
+                                   // set spreads over up to TERMS_SET_SPREAD slots per window of this region
     // Chunk plan of the long queries (more windows than one round): with
     // n_chunks > 0 every long query is processed by one CTA per round (its set
     // at tables + table_base[q] filled with EMPTY_KEY, ell[q] and long_flag[q]

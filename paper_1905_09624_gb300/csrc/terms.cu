@@ -26,6 +26,8 @@
 // (cleared by the caller) and appends to its global list, counting the
 // distinct terms with a global atomic; then one CTA per (query, group of
 // blocks) runs the row pass.  Without a chunk plan one CTA walks all rounds.
+#include <algorithm>
+
 #include "terms_common.cuh"
 
 namespace cobs {
@@ -192,10 +194,12 @@ constexpr uint32_t TERMS_GENERAL_BP = COBS_TERMS_GENERAL_BP;
 template <bool FAST>
 __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     constexpr uint32_t NBH = FAST ? 2 : TERMS_GENERAL_BP;  // histograms in shared memory
-    // dynamic shared memory: the on-chip set (smem_slots) and its distinct list
-    // (a set of cap <= smem_slots slots holds at most cap / 2 terms)
+    // dynamic shared memory: the on-chip table region (smem_table slots) and the
+    // distinct list (a set of set_slots(windows) <= smem_slots slots is for at
+    // most smem_slots / 2 windows)
     extern __shared__ unsigned long long s_table[];
-    unsigned long long *s_list = s_table + a.smem_slots;
+    const uint32_t table_slots = a.smem_table > a.smem_slots ? a.smem_table : a.smem_slots;
+    unsigned long long *s_list = s_table + table_slots;
     __shared__ __align__(16) uint8_t s_bytes[TERMS_STAGE_BYTES];
     __shared__ uint32_t s_pk[TERMS_PK_WORDS];   // 2-bit bases, 16 per word
     __shared__ uint16_t s_inv[TERMS_PK_WORDS];  // non-ACGT bytes, 16 per word
@@ -213,9 +217,15 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_query_terms(TermsArgs a) {
     const uint64_t npos = windows_of(a, q, &off0);
     if (a.n_chunks && npos > TERMS_ROUND) return;  // a long query of the chunk plan
     const uint32_t k = a.k;
-    const uint32_t cap = (uint32_t)set_slots(npos);
-    // a set that fits on chip holds at most TERMS_ROUND distinct terms (one round)
-    const bool in_smem = cap <= a.smem_slots;
+    // a set that fits on chip holds at most TERMS_ROUND distinct terms (one round);
+    // on chip it spreads over up to TERMS_SET_SPREAD slots per window
+    const bool in_smem = set_slots(npos) <= a.smem_slots;
+    uint32_t cap = (uint32_t)set_slots(npos);
+    if (in_smem) {
+        const uint32_t sparse = (uint32_t)npos * TERMS_SET_SPREAD;
+        const uint32_t wide = sparse < table_slots ? sparse : table_slots;
+        cap = wide > cap ? wide : cap;
+    }
     unsigned long long *table = in_smem ? s_table : a.tables + a.table_base[q];
     const uint64_t base = a.term_base[q];
     unsigned long long *list = in_smem ? s_list : a.codes + base;
@@ -392,13 +402,15 @@ void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s) 
     if (n_queries == 0) return;
     static PerDeviceOnce once;
     once([] {
-        const int most = (int)(TERMS_SMEM_SLOTS * 3 / 2 * sizeof(unsigned long long));
+        const int most = (int)std::max<size_t>(TERMS_SMEM_SLOTS * 3 / 2 * sizeof(unsigned long long),
+                                               TERMS_SMEM_BUDGET);
         cudaFuncSetAttribute(k_query_terms<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         cudaFuncSetAttribute(k_query_terms<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     });
-    // shared memory sized to the largest set of the launch that is kept on chip,
-    // plus its list of at most half as many terms
-    const size_t dyn = (size_t)(a.smem_slots + a.smem_slots / 2) * sizeof(unsigned long long);
+    // shared memory: the on-chip table region (at least the largest set of the
+    // launch that is kept on chip), plus a list of half that set's slots
+    const uint32_t table_slots = a.smem_table > a.smem_slots ? a.smem_table : a.smem_slots;
+    const size_t dyn = (size_t)(table_slots + a.smem_slots / 2) * sizeof(unsigned long long);
     if (a.h == 1 && a.n_blocks <= 2) k_query_terms<true><<<n_queries, TERMS_THREADS, dyn, s>>>(a);
     else k_query_terms<false><<<n_queries, TERMS_THREADS, dyn, s>>>(a);
     if (a.n_chunks) {
