@@ -757,9 +757,18 @@ def run_gpu(args):
         plain_res = eng.download_arrays()
         same = all(np.array_equal(a, b) for a, b in zip(plain_res, batched_res))
         pt = min(p["ms_total"] for p in pr) / 1e3
+        # the same batch in the plain form through the host-buffer API (H2D of the
+        # queries, one query per launch, D2H of the hits)
+        t0 = time.perf_counter()
+        plain_host = eng.query_host_arrays(pin_q, wl.q_off, wl.thresholds, cobs.COBS_PLAIN)
+        pe2e = time.perf_counter() - t0
+        same_host = all(np.array_equal(a, b) for a, b in zip(plain_host, batched_res))
         plain = {"value": pr[0]["terms"] / pt, "unit": UNIT, "ms": pt * 1e3,
+                 "us_per_query": pt * 1e6 / wl.n_queries,
                  "row_gbs_logical": pr[0]["row_bytes"] / pt / 1e9,
-                 "launches": pr[0]["launches"], "results_identical_to_batched": bool(same)}
+                 "launches": pr[0]["launches"], "results_identical_to_batched": bool(same and same_host),
+                 "e2e": {"value": pr[0]["terms"] / pe2e, "unit": UNIT, "ms": pe2e * 1e3,
+                         "h2d_bytes": h2d, "path": "query_host_arrays, plain form"}}
     # ---- hit emission under many hits: the first 1,000 queries at K = 1 permille
     # (min score 1: nearly every document is a hit) against the same queries at
     # the workload's thresholds, batched form, gather and hit phases
@@ -996,7 +1005,7 @@ def main():
     ap.add_argument("--cpu-queries", type=int, default=400)
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--ref-queries-per-step", type=int, default=40)
-    ap.add_argument("--serve-rates", default="1000,10000,50000",
+    ap.add_argument("--serve-rates", default="1000,5000,10000,20000,50000",
                     help="Poisson arrival rates (queries/s) of the serving run on the cfg2 index; '' to skip")
     ap.add_argument("--serve-seconds", type=float, default=1.5)
     ap.add_argument("--serve-inflight", type=int, default=3, help="waves on the device at once")

@@ -195,6 +195,45 @@ def test_errors():
     assert res == []
 
 
+def test_score_width_limits():
+    """16-bit scores count at most 65,535: a query of exactly 65,535 windows runs in
+    every form, and a document that holds it scores 65,535 (the largest 16-bit
+    value, nothing wraps); one window more is refused with OVERFLOW, and 2^24
+    windows (the batch plan's limit for any score width) with ARG."""
+    k = 31
+    lens = synth.lognormal_lengths(91, 40, 3000, 0.5, 500, 20000)
+    docs, off = synth.dna_docs(91, lens)
+    qmax = synth.dna_docs(92, [65535 + k - 1])[0].tobytes()
+    extra = [qmax, qmax[:30000] + bytes(docs[:2000])]   # the query itself, and half of it
+    db = np.concatenate([docs, np.frombuffer(b"".join(extra), np.uint8)])
+    doff = np.concatenate([off, off[-1] + np.cumsum([len(x) for x in extra]).astype(np.uint64)])
+    ql = [qmax, qmax[:40000], bytes(docs[int(off[3]):int(off[3]) + 900])]
+    qo = np.zeros(len(ql) + 1, np.uint64)
+    qo[1:] = np.cumsum([len(x) for x in ql])
+    qb = np.frombuffer(b"".join(ql), np.uint8)
+    thr = np.array([1000, 300, 500], np.uint16)
+    wl = synth.Workload("score-width", 0, k, 1, 0.3, 16, 16, db, doff, qb, qo, thr, np.full(len(ql), -1))
+    ref = oracle_index(wl)
+    dix = device_index(wl)
+    assert_index_equal(dix, ref)
+    ell, mn, ids, sc = ref.query(ql[0], 1000)
+    assert ell == 65535 and len(ids) >= 1 and int(sc[0]) == 65535 and int(ids[0]) == len(lens)
+    for flags in FORMS:
+        assert_results_equal(dix.query(qb, qo, thr, flags), ref, ql, thr)
+    over = np.frombuffer(qmax + b"A", np.uint8)
+    for flags in FORMS:
+        with pytest.raises(cobs.CobsError) as e:
+            dix.query(over, np.array([0, len(over)], np.uint64), np.array([500], np.uint16), flags)
+        assert e.value.status == cobs.COBS_ERR_OVERFLOW
+    wl32 = small_compact(seed=93, n_docs=30, n_q=2)
+    d32 = device_index(wl32)
+    huge = np.zeros((1 << 24) + k - 1, np.uint8)
+    huge[:] = ord("A")
+    with pytest.raises(cobs.CobsError) as e:
+        d32.query(huge, np.array([0, len(huge)], np.uint64), np.array([500], np.uint16), cobs.COBS_BATCHED)
+    assert e.value.status == cobs.COBS_ERR_ARG
+
+
 def test_empty_and_tiny_documents():
     docs = [b"", b"ACG", b"ACGTACGTACGTACGTACGTACGTACGTACGTAC", b"N" * 50, b"GATTACA" * 10]
     off = np.zeros(len(docs) + 1, np.uint64)
