@@ -57,16 +57,28 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_hits_scan(HitsArgs a) {
     if (threadIdx.x == 0) a.hit_off[n] = s_carry;
 }
 
+// Raw hits of one query arrive in runs (a warp tile emits its query's hits
+// together): the lanes of a warp holding the same query reserve their slots
+// with one atomic (one atomic per hit serialises on the query's cursor when a
+// query has thousands of hits).  Every lane of a warp runs the same iterations.
 __global__ void k_hits_scatter(HitsArgs a) {
     const unsigned long long total = *a.hit_count;
     // On overflow the offsets exceed the key buffer: leave it; the host re-runs
     // the batch with a larger capacity.
     if (total > a.hit_cap) return;
-    for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < total;
-         r += (unsigned long long)gridDim.x * blockDim.x) {
-        uint32_t q = a.raw_q[r];
-        unsigned long long pos = a.hit_off[q] + atomicAdd(&a.qcursor[q], 1u);
-        a.keys[pos] = a.raw_key[r];
+    const uint32_t lane = threadIdx.x & 31u;
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long w0 = ((unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+         w0 < total; w0 += warps * 32) {
+        const unsigned long long r = w0 + lane;
+        const bool act = r < total;
+        const uint32_t q = act ? a.raw_q[r] : 0xFFFFFFFFu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, q);
+        const uint32_t leader = __ffs(peers) - 1;
+        uint32_t first = 0;
+        if (act && lane == leader) first = atomicAdd(&a.qcursor[q], (uint32_t)__popc(peers));
+        first = __shfl_sync(0xffffffffu, first, leader);
+        if (act) a.keys[a.hit_off[q] + first + __popc(peers & ((1u << lane) - 1u))] = a.raw_key[r];
     }
 }
 

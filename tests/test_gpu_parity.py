@@ -87,6 +87,23 @@ def test_many_hits_large_segments():
     assert_results_equal(got, ref, wl.query_list(), thr, which=range(0, wl.n_queries, 7))
 
 
+@pytest.mark.parametrize("n_docs", [1024, 1025, 2049, 30000])
+def test_many_hits_sort_limits(n_docs):
+    # K = 1 permille and 400-base queries: every document is a hit.  1,024 hits
+    # is the most one query's shared-memory sort takes; 1,025 goes to the
+    # large-segment sort as one chunk; 2,049 is a full 2,048-key chunk, a one-key
+    # chunk and a merge pass in global memory; 30,000 is 15 chunks and four passes.
+    wl = small_compact(seed=41, n_docs=n_docs, median=300, sigma=0.3, lo=100, hi=1000, block_docs=4096, n_q=6,
+                       q_len=400)
+    ref = oracle_index(wl)
+    dix = device_index(wl)
+    thr = np.full(wl.n_queries, 1, np.uint16)
+    for flags in (cobs.COBS_BATCHED, cobs.COBS_GRAPH):
+        got = dix.query(wl.queries, wl.q_off, thr, flags)
+        assert max(len(g[2]) for g in got) == n_docs
+        assert_results_equal(got, ref, wl.query_list(), thr)
+
+
 def test_hit_capacity_overflow_reruns(compact):
     wl, ref, dix = compact
     eng = cobs.Engine(dix, max_hits=4)
