@@ -411,8 +411,9 @@ static cobs_status ensure_buffers(cobs_engine *eng, const BatchPlan &bp) {
     CU(eng->long_flag.ensure(n * 4));
     CU(eng->ell.ensure(n * 4));
     CU(eng->minsc.ensure(n * 4));
-    // qcount, then the counters (one memset clears both): [0] hits, [1..14] work
-    // counters, [15] big segments, then 4 per block for a streamed index
+    // qcount, then the counters (one memset clears both): [0] hits, [1..4] work
+    // counters, [13] and [15] the hit lists to sort, [14] the gather's error
+    // flag, then 4 per block for a streamed index
     CU(eng->qcount.ensure(n * 4 + (64 + 4 * std::max<uint64_t>(nb, stream_units(eng->dix))) * 8));
     CU(eng->qcursor.ensure(n * 4));
     CU(eng->biglist.ensure(n * 4));
@@ -729,6 +730,7 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
     ha.out_scores = eng->out_scores.as<uint32_t>();
     ha.big_list = eng->biglist.as<uint32_t>();
     ha.big_count = ctr + 15;  // cleared with the other counters
+    ha.mid_count = ctr + 13;
     {
         TraceRange tr_hits("cobs.hits");
         launch_hits_finalize(ha, s);

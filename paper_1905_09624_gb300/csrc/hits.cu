@@ -2,59 +2,93 @@
 // per-query lists sorted by score descending, then original id ascending
 // (Sec. 2.3 "Parallelization": scores of disjoint partitions, then the top scores
 // are selected).  Key = (~score << 32) | id, so ascending keys give that order.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace cobs {
 
 constexpr uint32_t SCAN_THREADS = 1024;
+constexpr uint32_t SCAN_PER = 8;  // rows of SCAN_THREADS queries whose inputs are loaded together
 constexpr uint32_t SORT_THREADS = 128;
 constexpr uint32_t SORT_SMEM_KEYS = 1024;
 
 // Exclusive scan of the per-query hit counts (one CTA), threshold per query,
-// reset of the scatter cursors.  The CTA walks the queries in tiles of
-// SCAN_THREADS, one query per thread (coalesced), scans each tile by warp
-// shuffles and the warps' sums, and carries the running total to the next tile.
+// reset of the scatter cursors, and the lists of queries to sort: those with
+// more than SORT_SMEM_KEYS hits from the front of big_list, those with 1 to
+// SORT_SMEM_KEYS from its back.  The CTA walks the queries in rows of
+// SCAN_THREADS, one query per thread (coalesced); the inputs of SCAN_PER rows
+// are loaded together first.  Each row is one scan (warp shuffles, then the
+// warps' sums) of a 64-bit value that packs the query's hit count above two
+// 11-bit flags (large list, small list), so the scan gives the hit offset and
+// both list positions at once; running totals carry to the next row.
 __global__ void __launch_bounds__(SCAN_THREADS) k_hits_scan(HitsArgs a) {
     constexpr uint32_t NW = SCAN_THREADS / 32;
+    constexpr uint32_t FB = 11;  // bits of a row's count of listed queries (at most SCAN_THREADS)
+    static_assert(SCAN_THREADS < (1u << FB), "list counts of a row fit their fields");
+    constexpr unsigned long long FMASK = (1ULL << FB) - 1ULL;
     __shared__ unsigned long long s_warp[NW];
-    __shared__ unsigned long long s_carry;
+    __shared__ unsigned long long s_carry, s_big, s_mid;
     const uint32_t n = a.n_queries;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
-    for (uint32_t t0 = 0; t0 < n; t0 += SCAN_THREADS) {
-        const uint32_t q = t0 + threadIdx.x;
-        const uint32_t c = q < n ? a.qcount[q] : 0u;
-        unsigned long long incl = c;
+    if (threadIdx.x == 0) { s_carry = 0; s_big = 0; s_mid = 0; }
+    for (uint32_t t0 = 0; t0 < n; t0 += SCAN_THREADS * SCAN_PER) {
+        uint32_t c[SCAN_PER], ms[SCAN_PER];
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, d);
-            if ((int)lane >= d) incl += y;
+        for (uint32_t i = 0; i < SCAN_PER; i++) {
+            const uint32_t q = t0 + i * SCAN_THREADS + threadIdx.x;
+            c[i] = q < n ? a.qcount[q] : 0u;
+            ms[i] = q < n ? (uint32_t)(((uint64_t)a.thr[q] * a.ell[q] + 999u) / 1000u) : 0u;
         }
-        if (lane == 31u) s_warp[warp] = incl;
-        __syncthreads();  // warp sums written; s_carry of the previous tile final
-        if (warp == 0) {
-            unsigned long long w = lane < NW ? s_warp[lane] : 0ULL;
+#pragma unroll
+        for (uint32_t i = 0; i < SCAN_PER; i++) {
+            const uint32_t q = t0 + i * SCAN_THREADS + threadIdx.x;
+            if (t0 + i * SCAN_THREADS >= n) break;  // the same for every thread
+            const bool big = c[i] > SORT_SMEM_KEYS;
+            const bool mid = c[i] > 0u && !big;
+            const unsigned long long v =
+                ((unsigned long long)c[i] << (2 * FB)) | ((unsigned long long)big << FB) | (unsigned long long)mid;
+            unsigned long long incl = v;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                const unsigned long long y = __shfl_up_sync(0xffffffffu, w, d);
-                if ((int)lane >= d) w += y;
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, d);
+                if ((int)lane >= d) incl += y;
             }
-            if (lane < NW) s_warp[lane] = w;  // inclusive sums of the warps
+            if (lane == 31u) s_warp[warp] = incl;
+            __syncthreads();  // warp sums written; the carries of the previous row final
+            if (warp == 0) {
+                unsigned long long w = lane < NW ? s_warp[lane] : 0ULL;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const unsigned long long y = __shfl_up_sync(0xffffffffu, w, d);
+                    if ((int)lane >= d) w += y;
+                }
+                if (lane < NW) s_warp[lane] = w;  // inclusive sums of the warps
+            }
+            __syncthreads();
+            const unsigned long long row_total = s_warp[NW - 1];
+            const unsigned long long excl = (warp ? s_warp[warp - 1] : 0ULL) + incl - v;
+            if (big) a.big_list[s_big + ((excl >> FB) & FMASK)] = q;
+            if (mid) a.big_list[n - 1u - (uint32_t)(s_mid + (excl & FMASK))] = q;
+            if (q < n) {
+                a.hit_off[q] = s_carry + (excl >> (2 * FB));
+                a.qcursor[q] = 0;
+                a.min_score[q] = ms[i];
+            }
+            __syncthreads();  // every thread read the carries and s_warp
+            if (threadIdx.x == 0) {
+                s_carry += row_total >> (2 * FB);
+                s_big += (row_total >> FB) & FMASK;
+                s_mid += row_total & FMASK;
+            }
         }
-        __syncthreads();
-        const unsigned long long tile_total = s_warp[NW - 1];
-        const unsigned long long before = s_carry + (warp ? s_warp[warp - 1] : 0ULL);
-        if (q < n) {
-            a.hit_off[q] = before + incl - c;
-            if (c > SORT_SMEM_KEYS) a.big_list[atomicAdd(a.big_count, 1ULL)] = q;
-            a.qcursor[q] = 0;
-            a.min_score[q] = (uint32_t)(((uint64_t)a.thr[q] * a.ell[q] + 999u) / 1000u);
-        }
-        __syncthreads();  // every thread read s_carry and s_warp
-        if (threadIdx.x == 0) s_carry += tile_total;
     }
     __syncthreads();
-    if (threadIdx.x == 0) a.hit_off[n] = s_carry;
+    if (threadIdx.x == 0) {
+        a.hit_off[n] = s_carry;
+        *a.big_count = s_big;
+        *a.mid_count = s_mid;
+    }
 }
 
 // Raw hits of one query arrive in runs (a warp tile emits its query's hits
@@ -125,25 +159,29 @@ __device__ __forceinline__ void unpack(const unsigned long long *src, uint32_t n
     }
 }
 
-// One CTA per query with at most SORT_SMEM_KEYS hits: sort in shared memory.
+// Queries with 1 to SORT_SMEM_KEYS hits (listed from the back of big_list by
+// k_hits_scan), a fixed grid looping over them: sort in shared memory.
 __global__ void __launch_bounds__(SORT_THREADS) k_hits_segsort(HitsArgs a) {
     __shared__ unsigned long long sA[SORT_SMEM_KEYS];
     __shared__ unsigned long long sB[SORT_SMEM_KEYS];
-    const uint32_t q = blockIdx.x;
     unsigned long long total = *a.hit_count;
     if (total > a.hit_cap) return;  // the host re-runs with a larger capacity
-    const uint64_t o = a.hit_off[q];
-    const uint32_t n = (uint32_t)(a.hit_off[q + 1] - o);
-    if (n == 0 || n > SORT_SMEM_KEYS) return;  // larger segments: k_hits_segsort_big
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) sA[i] = a.keys[o + i];
-    __syncthreads();
-    unsigned long long *src = sA, *dst = sB;
-    for (uint32_t w = 1; w < n; w <<= 1) {
-        merge_pass(src, dst, n, w);
+    const unsigned long long nmid = *a.mid_count;
+    for (unsigned long long k = blockIdx.x; k < nmid; k += gridDim.x) {
+        const uint32_t q = a.big_list[a.n_queries - 1u - (uint32_t)k];
+        const uint64_t o = a.hit_off[q];
+        const uint32_t n = (uint32_t)(a.hit_off[q + 1] - o);
+        __syncthreads();  // the previous query's keys are unpacked
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) sA[i] = a.keys[o + i];
         __syncthreads();
-        unsigned long long *t = src; src = dst; dst = t;
+        unsigned long long *src = sA, *dst = sB;
+        for (uint32_t w = 1; w < n; w <<= 1) {
+            merge_pass(src, dst, n, w);
+            __syncthreads();
+            unsigned long long *t = src; src = dst; dst = t;
+        }
+        unpack(src, n, o, a.out_ids, a.out_scores);
     }
-    unpack(src, n, o, a.out_ids, a.out_scores);
 }
 
 // Merge-path split of the output diagonal d of merging sorted A[0..na) and
@@ -222,7 +260,11 @@ void launch_hits_finalize(const HitsArgs &a, cudaStream_t s) {
     if (a.n_queries == 0) return;
     k_hits_scan<<<1, SCAN_THREADS, 0, s>>>(a);
     k_hits_scatter<<<264, 256, 0, s>>>(a);
-    k_hits_segsort<<<a.n_queries, SORT_THREADS, 0, s>>>(a);
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t sort_grid = (uint32_t)std::min<uint64_t>(a.n_queries, (uint64_t)n_sm * 8);
+    k_hits_segsort<<<sort_grid, SORT_THREADS, 0, s>>>(a);
     const uint32_t grid = a.n_queries < 304 ? a.n_queries : 304;
     k_hits_segsort_big<<<grid, BIG_SORT_THREADS, 0, s>>>(a);
 }

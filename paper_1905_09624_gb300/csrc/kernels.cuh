@@ -228,8 +228,10 @@ struct HitsArgs {
     unsigned long long *tmp;       // sort scratch (same size)
     uint32_t *out_ids;
     uint32_t *out_scores;
-    uint32_t *big_list;            // scratch, n_queries entries: queries with many hits
-    unsigned long long *big_count; // zeroed before the launch
+    uint32_t *big_list;            // scratch, n_queries entries: queries with many hits from the front,
+                                   // queries with a few hits from the back
+    unsigned long long *big_count; // list lengths, written by the offset scan
+    unsigned long long *mid_count;
 };
 void launch_hits_finalize(const HitsArgs &a, cudaStream_t s);
 

@@ -223,6 +223,7 @@ extern "C" cobs_status cobs_query_one_noalloc(cobs_device_index *dix, const uint
     ha.out_scores = out_scores_dev;
     ha.big_list = reinterpret_cast<uint32_t *>(S + OFF_CURSOR + 4);
     ha.big_count = reinterpret_cast<unsigned long long *>(S + OFF_CTR + 128);  // cleared above
+    ha.mid_count = reinterpret_cast<unsigned long long *>(S + OFF_CTR + 136);
     launch_hits_finalize(ha, s);
     // number of hits = hit_off[1] (low 32 bits; at most the number of documents)
     NA_CU(cudaMemcpyAsync(out_meta_dev + 2, S + OFF_HITOFF + 8, 4, cudaMemcpyDeviceToDevice, s));
