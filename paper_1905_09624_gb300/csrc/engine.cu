@@ -735,7 +735,7 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
         TraceRange tr_hits("cobs.hits");
         launch_hits_finalize(ha, s);
     }
-    eng->stat_launches += 3;
+    eng->stat_launches += 4;  // offsets, scatter, the two segment sorts
     CU(cudaGetLastError());
     if (timed) CU(cudaEventRecordWithFlags(eng->ev[3], s, tflag));
     // hit count and the gather's wait-limit flag, read when the batch is collected
