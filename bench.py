@@ -819,10 +819,27 @@ def run_gpu(args):
         slot = (slot + 255) // 256 * 256
         n_slots = min(len(info["blocks"]), args.stage_bytes // slot if args.stage_bytes else 2)
         sm = float(np.mean(s_ms))
+        # the host link's ceiling: one 512 MB copy from pinned memory, best of 5
+        lk_h = torch.empty(512 << 20, dtype=torch.uint8, pin_memory=True)
+        lk_d = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+        lk = []
+        with torch.cuda.stream(stream):
+            for i in range(6):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                lk_d.copy_(lk_h, non_blocking=True)
+                e1.record(stream)
+                e1.synchronize()
+                if i:
+                    lk.append(e0.elapsed_time(e1))
+        link_gbs = lk_d.numel() / (min(lk) / 1e3) / 1e9
+        del lk_h, lk_d
+        h2d_gbs = sst["h2d_index_bytes"] / (sm / 1e3) / 1e9
         streamed = {"value": s_terms / args.streamed_steps / (sm / 1e3), "unit": UNIT, "ms_per_step": sm,
                     "steps": args.streamed_steps, "h2d_index_bytes_per_step": sst["h2d_index_bytes"],
-                    "h2d_index_gbs": sst["h2d_index_bytes"] / (sm / 1e3) / 1e9, "stage_slots": n_slots,
-                    "rows_host_numa_node": sst["stream_numa_node"],
+                    "h2d_index_gbs": h2d_gbs, "link_gbs": link_gbs, "link_frac": h2d_gbs / link_gbs,
+                    "link_rule": "index bytes copied per step / step time, over one 512 MB pinned copy's rate",
+                    "stage_slots": n_slots, "rows_host_numa_node": sst["stream_numa_node"],
                     "stage_bytes": n_slots * slot, "index_bytes": info["rows_bytes"],
                     "results_identical_to_resident": bool(same)}
         del seng, sdix
