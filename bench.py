@@ -168,9 +168,10 @@ def traffic_record(kernel_srcs, record="gather_batched_cfg2_dram.txt"):
     if kv.get("kernel_sources_sha256_16") != digest:
         return None
     try:
+        opt = lambda k: float(kv[k]) if k in kv else None  # noqa: E731  (L2 figures: not in every record)
         return {"dram_bytes": float(kv["dram_bytes_per_launch_full"]),
-                "l2_hit_pct": float(kv["lts_t_sector_hit_rate_pct"]),
-                "l2_sector_lookups_pct_of_peak": float(kv["lts_t_sectors_srcunit_tex_pct_of_peak"]),
+                "l2_hit_pct": opt("lts_t_sector_hit_rate_pct"),
+                "l2_sector_lookups_pct_of_peak": opt("lts_t_sectors_srcunit_tex_pct_of_peak"),
                 "slice_bytes": int(kv.get("slice_bytes", "128"))}
     except (KeyError, ValueError):
         return None
@@ -385,6 +386,7 @@ def run_serve(dix, wl, rates, seconds, verify_oracle=None, inflight=3, wave_max=
 # ------------------------------------------------------------ other configs
 CONFIG_RECORDS = {  # committed ncu records of the gather on a config's full workload
     "cfg4": ("gather_pipe_h3_cfg4_dram.txt", ["gather_h.cu", "gather_common.cuh"]),
+    "cfg3": ("gather_pipe_cfg3_dram.txt", ["gather.cu", "gather_common.cuh"]),
 }
 PLAIN_SAMPLE = {"cfg1": 200, "cfg3": 1000, "cfg4": 10000}   # queries run in the plain form
 ORACLE_SAMPLE = {"cfg1": 200, "cfg4": 200}                 # queries compared with the oracle
@@ -489,7 +491,8 @@ def measure_config(name, args, cobs, torch, stream, flush, device, hbm_peak, l2_
         csrc = os.path.join(ROOT, "paper_1905_09624_gb300", "csrc")
         rec = traffic_record([os.path.join(csrc, f) for f in rec_name[1]], rec_name[0])
     out["row_gbs_physical"] = rec["dram_bytes"] / g_step / 1e9 if rec else None
-    out["physical_note"] = (f"ncu DRAM bytes of one launch (profiles/{rec_name[0]}) over the live gather time"
+    out["physical_note"] = (f"ncu DRAM bytes of one step's gather launches (profiles/{rec_name[0]}) over the "
+                            "live gather time"
                             if rec else "no current ncu record of this workload's gather")
     del eng, sub_q, sub_off, sub_thr, d_q, d_off, d_thr
     ns = ORACLE_SAMPLE.get(name, 0)

@@ -39,3 +39,19 @@ def test_traffic_record_matches_the_gather_sources():
     assert rec is not None, "gather sources changed since profiles/gather_batched_cfg2_dram.txt was captured"
     assert rec["slice_bytes"] in (128, 256)
     assert 0.6e9 < rec["dram_bytes"] < 12.26e9  # at least the index once, at most the logical row bytes
+
+
+def test_config_traffic_records_match_their_sources():
+    # the records behind the configs object's physical row GB/s (cfg3: one
+    # step's four class launches; cfg4: one launch) match the current kernels
+    # and hold between the index once and the logical row bytes
+    sys.path.insert(0, ROOT)
+    import bench
+    csrc = os.path.join(ROOT, "paper_1905_09624_gb300", "csrc")
+    bounds = {"cfg3": (8.0e9, 3.77e12), "cfg4": (0.47e9, 5.03e11)}
+    for name, (record, srcs) in bench.CONFIG_RECORDS.items():
+        rec = bench.traffic_record([os.path.join(csrc, f) for f in srcs], record)
+        assert rec is not None, f"{name}: kernel sources changed since profiles/{record} was captured"
+        lo, hi = bounds[name]
+        assert lo < rec["dram_bytes"] < hi, (name, rec)
+
