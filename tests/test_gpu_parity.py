@@ -104,6 +104,35 @@ def test_many_hits_sort_limits(n_docs):
         assert_results_equal(got, ref, wl.query_list(), thr)
 
 
+def test_counter_class_and_round_boundaries():
+    # Queries of exactly 1, 255, 256, 2,048, 2,049, 4,095, 4,096, 65,535 and
+    # 65,536 windows (random bases: as many distinct terms), each also a document,
+    # so the best score of each query is its whole term count: the largest value
+    # of the 8-, 12- and 16-level counters (255, 4,095, 65,535) and one more, and
+    # the last on-chip term set (2,048 windows) and the first long query's chunks.
+    # Every form, K = 1000 and 500 permille.
+    k = 31
+    windows = [1, 255, 256, 2048, 2049, 4095, 4096, 65535, 65536]
+    qs = [synth.dna_docs(95 + i, [w + k - 1])[0].tobytes() for i, w in enumerate(windows)]
+    lens = synth.lognormal_lengths(94, 30, 3000, 0.5, 500, 20000)
+    docs, off = synth.dna_docs(94, lens)
+    db = np.concatenate([docs, np.frombuffer(b"".join(qs), np.uint8)])
+    doff = np.concatenate([off, off[-1] + np.cumsum([len(x) for x in qs]).astype(np.uint64)])
+    ql = qs + qs
+    qo = np.zeros(len(ql) + 1, np.uint64)
+    qo[1:] = np.cumsum([len(x) for x in ql])
+    qb = np.frombuffer(b"".join(ql), np.uint8)
+    thr = np.array([1000] * len(qs) + [500] * len(qs), np.uint16)
+    wl = synth.Workload("boundaries", 0, k, 1, 0.3, 16, 32, db, doff, qb, qo, thr, np.full(len(ql), -1))
+    ref = oracle_index(wl)
+    dix = device_index(wl)
+    for i, w in enumerate(windows):
+        ell, mn, ids, sc = ref.query(qs[i], 1000)
+        assert ell == w and int(sc[0]) == w and len(lens) + i in ids.tolist()
+    for flags in FORMS:
+        assert_results_equal(dix.query(qb, qo, thr, flags), ref, ql, thr)
+
+
 def test_hit_capacity_overflow_reruns(compact):
     wl, ref, dix = compact
     eng = cobs.Engine(dix, max_hits=4)

@@ -144,6 +144,27 @@ def test_noalloc_matches_batched_per_index_kind(make):
         assert _same(got, ref[i]), (i, got[:2], ref[i][:2])
 
 
+def test_noalloc_at_its_window_limit():
+    # exactly COBS_NOALLOC_MAX_WINDOWS (16,384) windows: answered, as the batched
+    # form; one window more: refused
+    import torch
+    torch.cuda.set_device(0)
+    wl = small_compact(seed=65, n_docs=400, block_docs=128, n_q=2, q_len=300)
+    dix = device_index(wl)
+    k = 31
+    q = synth.dna_docs(66, [16384 + k - 1])[0].tobytes()
+    qb, qo, thr = _batch([q], [300])
+    ref = dix.query(qb, qo, thr, cobs.COBS_BATCHED)
+    got = _run_noalloc(dix, wl.n_docs, q, 300)
+    assert got[0] == 16384 and _same(got, ref[0])
+    L = cobs.lib()
+    over = torch.from_numpy(np.frombuffer(q + b"A", np.uint8).copy()).cuda()
+    out = torch.zeros(max(wl.n_docs, 3), dtype=torch.int32, device="cuda")
+    st = int(L.cobs_query_one_noalloc(dix.h, over.data_ptr(), len(q) + 1, 300, out.data_ptr(), out.data_ptr(),
+                                      out.data_ptr(), wl.n_docs, None))
+    assert st == cobs.COBS_ERR_ARG and b"windows" in L.cobs_last_error()
+
+
 def test_noalloc_rejects_beyond_its_limits():
     import torch
     torch.cuda.set_device(0)
