@@ -384,6 +384,7 @@ def run_serve(dix, wl, rates, seconds, verify_oracle=None, inflight=3, wave_max=
 
 
 # ------------------------------------------------------------ other configs
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy peak is the roofline)
 CONFIG_RECORDS = {  # committed ncu records of the gather on a config's full workload
     "cfg4": ("gather_pipe_h3_cfg4_dram.txt", ["gather_h.cu", "gather_common.cuh"]),
     "cfg3": ("gather_pipe_cfg3_dram.txt", ["gather.cu", "gather_common.cuh"]),
@@ -934,6 +935,8 @@ def run_gpu(args):
                 "launch_ms": g_ms, "bytes_rule": "sum over distinct query terms and blocks of h * rowbytes_b",
                 "dram_gbs": dram_gbs, "dram_frac": dram_gbs / peak if dram_gbs else None,
                 "hbm_peak": peak, "hbm_peak_kind": hbm_kind,
+                "dram_frac_of_nominal": dram_gbs / HBM_NOMINAL_GBS if dram_gbs else None,
+                "hbm_nominal": HBM_NOMINAL_GBS,
                 "reuse": achieved / peak if achieved else None,
                 "reuse_rule": "logical row bytes per second over the HBM peak: above 1 only through L2 reuse",
                 "l2_hit_pct": rec["l2_hit_pct"] if rec else None,
