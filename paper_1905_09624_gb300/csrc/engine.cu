@@ -265,14 +265,11 @@ static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n
         bp.tcap += (np + TERM_ALIGN - 1) / TERM_ALIGN * TERM_ALIGN;
         uint64_t sl = set_slots(np);
         // a global set for every query whose set does not fit on chip and for
-        // every query of more than one round (chunk CTAs share its set)
-        if (sl > TERMS_SMEM_SLOTS || np > terms_round_windows()) {
-            bp.table_base[q] = bp.total_slots;
-            bp.total_slots += sl;
-        } else {
-            bp.table_base[q] = 0;
+        // every query of more than one round (chunk CTAs share its set): placed
+        // with the long-query groups below
+        bp.table_base[q] = 0;
+        if (sl <= TERMS_SMEM_SLOTS && np <= terms_round_windows())
             bp.smem_slots = std::max<uint32_t>(bp.smem_slots, (uint32_t)sl);
-        }
         bp.sum_npos += np;
         bp.max_npos = std::max(bp.max_npos, np);
     }
@@ -288,13 +285,31 @@ static cobs_status make_plan(cobs_engine *eng, const uint64_t *h_off, uint64_t n
     bp.long_q.clear();
     bp.chunk_q.clear();
     bp.chunk_w0.clear();
+    bp.long_groups.clear();
+    bp.total_slots = 0;
     const uint64_t round = terms_round_windows();
+    uint64_t region = TERMS_TABLE_REGION_SLOTS;
+    for (uint64_t q = 0; q < n; q++)
+        if (bp.npos[q] > round) region = std::max<uint64_t>(region, set_slots(bp.npos[q]));
+    uint64_t used = 0;  // slots of the current group
     for (uint64_t q = 0; q < n; q++) {
         if (bp.npos[q] <= round) continue;
+        const uint64_t sl = set_slots(bp.npos[q]);
+        if (bp.long_groups.empty() || used + sl > region) {
+            bp.long_groups.push_back({(uint32_t)bp.long_q.size(), 0u, (uint32_t)bp.chunk_q.size(), 0u, 0});
+            used = 0;
+        }
+        BatchPlan::LongGroup &g = bp.long_groups.back();
+        bp.table_base[q] = used;
+        used += sl;
+        g.slots = used;
+        g.n_long += 1;
+        bp.total_slots = std::max(bp.total_slots, used);
         bp.long_q.push_back((uint32_t)q);
         for (uint64_t w0 = 0; w0 < bp.npos[q]; w0 += round) {
             bp.chunk_q.push_back((uint32_t)q);
             bp.chunk_w0.push_back((uint32_t)w0);
+            g.n_chunks += 1;
         }
     }
     // queries by windows, longest first, ties in input order: a stable LSD radix
@@ -568,9 +583,10 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
     } else {
         ta.q0 = 0;
         if (!bp.long_q.empty()) {
-            // long queries: sets cleared, distinct counts and flags zeroed, then a
-            // CTA per chunk and a CTA per (query, block group)
-            CU(cudaMemsetAsync(eng->tables.p, 0xFF, bp.total_slots * 8, s));
+            // long queries: distinct counts and flags zeroed; after the one-CTA-
+            // per-query kernel, group by group the table region is cleared and a
+            // CTA per chunk inserts (a group's sets stay in L2), then a CTA per
+            // (query, block group) runs the row pass
             CU(cudaMemsetAsync(eng->ell.p, 0, n * 4, s));
             CU(cudaMemsetAsync(eng->long_flag.p, 0, n * 4, s));
             ta.long_q = long_q;
@@ -579,13 +595,25 @@ static cobs_status enqueue(cobs_engine *eng, const uint8_t *d_bytes, const uint6
             ta.long_flag = eng->long_flag.as<uint32_t>();
             ta.n_long = (uint32_t)bp.long_q.size();
             ta.n_chunks = (uint32_t)bp.chunk_q.size();
-            eng->stat_launches += 2;
         }
         {
             TraceRange tr_terms("cobs.terms");
-            launch_query_terms(ta, (uint32_t)n, s);
+            launch_terms_short(ta, (uint32_t)n, s);
+            eng->stat_launches += 1;
+            for (const BatchPlan::LongGroup &g : bp.long_groups) {
+                CU(cudaMemsetAsync(eng->tables.p, 0xFF, g.slots * 8, s));
+                TermsArgs tg = ta;
+                tg.chunk_q = chunk_q + g.chunk0;
+                tg.chunk_w0 = chunk_w0 + g.chunk0;
+                tg.n_chunks = g.n_chunks;
+                launch_terms_long_insert(tg, s);
+                eng->stat_launches += 1;
+            }
+            if (!bp.long_q.empty()) {
+                launch_terms_long_rows(ta, s);
+                eng->stat_launches += 1;
+            }
         }
-        eng->stat_launches += 1;
         CU(cudaGetLastError());
         if (timed) CU(cudaEventRecordWithFlags(eng->ev[1], s, tflag));
         const uint32_t qpw = 32 / eng->lanes_per_query;
@@ -774,7 +802,12 @@ static std::vector<uint64_t> graph_signature(cobs_engine *eng, const uint8_t *d_
                                  (uint64_t)eng->pin_count.p, (uint64_t)eng->slices.p, eng->n_slices,
                                  (uint64_t)bp.items.size(), (uint64_t)bp.split.size(), bp.n_parts,
                                  (uint64_t)eng->partials.p, (uint64_t)bp.long_q.size(), (uint64_t)bp.chunk_q.size(),
-                                 (uint64_t)eng->long_flag.p, eng->cfg.class_streams, bp.part_terms};
+                                 (uint64_t)eng->long_flag.p, eng->cfg.class_streams, bp.part_terms,
+                                 (uint64_t)bp.long_groups.size()};
+    for (const auto &g : bp.long_groups) {
+        sig.push_back(g.n_chunks);
+        sig.push_back(g.slots);
+    }
     for (const auto &c : bp.classes) {
         sig.push_back(c.begin);
         sig.push_back(c.count);

@@ -114,6 +114,14 @@ struct BatchPlan {
     // long queries (more windows than one round of the term kernel): one term
     // CTA per round (chunk), then one row CTA per (query, block group)
     std::vector<uint32_t> long_q, chunk_q, chunk_w0;
+    // consecutive long queries whose sets share the table region in turn: the
+    // sets of a group sit at table_base[q] within the region (cleared before the
+    // group inserts)
+    struct LongGroup {
+        uint32_t long0, n_long, chunk0, n_chunks;
+        uint64_t slots;
+    };
+    std::vector<LongGroup> long_groups;
     uint64_t tcap = 0, total_slots = 0, sum_npos = 0, max_npos = 0;
     uint32_t smem_slots = 16;  // largest distinct set of the batch kept in shared memory
 };

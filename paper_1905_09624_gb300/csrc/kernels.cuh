@@ -85,7 +85,18 @@ struct TermsArgs {
     uint32_t n_long, n_chunks;
 };
 void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s);
+// The three parts of launch_query_terms, for callers that clear the long
+// queries' sets group by group: the one-CTA-per-query kernel (long queries of
+// the chunk plan return at once), the insertion of a.n_chunks chunks, the row
+// pass of a.n_long long queries.
+void launch_terms_short(const TermsArgs &a, uint32_t n_queries, cudaStream_t s);
+void launch_terms_long_insert(const TermsArgs &a, cudaStream_t s);
+void launch_terms_long_rows(const TermsArgs &a, cudaStream_t s);
 uint32_t terms_round_windows();    // windows per round (long queries have more)
+// The global sets of a batch's long queries are filled group by group in one
+// region of this many slots (64 MB: it stays in L2 while a group inserts), or
+// of the largest single set when that is larger.
+constexpr uint64_t TERMS_TABLE_REGION_SLOTS = 8ULL << 20;
 
 // Batched gather/AND/ADD with fused threshold (persistent).
 struct SliceDesc {

@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(TERMS_THREADS) k_terms_long_rows(TermsArgs a) 
     }
 }
 
-void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s) {
+void launch_terms_short(const TermsArgs &a, uint32_t n_queries, cudaStream_t s) {
     if (n_queries == 0) return;
     static PerDeviceOnce once;
     once([] {
@@ -413,10 +413,23 @@ void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s) 
     const size_t dyn = (size_t)(table_slots + a.smem_slots / 2) * sizeof(unsigned long long);
     if (a.h == 1 && a.n_blocks <= 2) k_query_terms<true><<<n_queries, TERMS_THREADS, dyn, s>>>(a);
     else k_query_terms<false><<<n_queries, TERMS_THREADS, dyn, s>>>(a);
+}
+
+void launch_terms_long_insert(const TermsArgs &a, cudaStream_t s) {
+    if (a.n_chunks) k_terms_long_insert<<<a.n_chunks, TERMS_THREADS, 0, s>>>(a);
+}
+
+void launch_terms_long_rows(const TermsArgs &a, cudaStream_t s) {
+    const uint32_t groups = (a.n_blocks + BP - 1) / BP;
+    if (a.n_long && groups) k_terms_long_rows<<<dim3(a.n_long, groups), TERMS_THREADS, 0, s>>>(a);
+}
+
+void launch_query_terms(const TermsArgs &a, uint32_t n_queries, cudaStream_t s) {
+    if (n_queries == 0) return;
+    launch_terms_short(a, n_queries, s);
     if (a.n_chunks) {
-        k_terms_long_insert<<<a.n_chunks, TERMS_THREADS, 0, s>>>(a);
-        const uint32_t groups = (a.n_blocks + BP - 1) / BP;
-        if (groups) k_terms_long_rows<<<dim3(a.n_long, groups), TERMS_THREADS, 0, s>>>(a);
+        launch_terms_long_insert(a, s);
+        launch_terms_long_rows(a, s);
     }
 }
 

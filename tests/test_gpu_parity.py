@@ -133,6 +133,24 @@ def test_counter_class_and_round_boundaries():
         assert_results_equal(dix.query(qb, qo, thr, flags), ref, ql, thr)
 
 
+def test_long_queries_in_several_set_groups():
+    # 130 queries of 40,000 bases: their global distinct-term sets (2 slots per
+    # window, 10.4 M slots) exceed the 8 M-slot table region, so the batch
+    # inserts them in two groups that reuse the region in turn
+    k = 31
+    lens = synth.lognormal_lengths(97, 200, 20000, 0.5, 2000, 200000)
+    docs, off = synth.dna_docs(97, lens)
+    qb, qo, src = synth.dna_queries(98, 130, docs, off, n_tp=80, fixed_len=40000, rate_lo=0.0, rate_hi=0.02)
+    ql = [bytes(qb[qo[i]:qo[i + 1]]) for i in range(130)]
+    assert sum(2 * (len(x) - k + 1) for x in ql) > (8 << 20)
+    thr = synth.choice_u16(99, 130, [300, 700, 1000])
+    wl = synth.Workload("long-groups", 0, k, 1, 0.3, 64, 32, docs, off, qb, qo, thr, src)
+    ref = oracle_index(wl)
+    dix = device_index(wl)
+    for flags in (cobs.COBS_BATCHED, cobs.COBS_GRAPH):
+        assert_results_equal(dix.query(qb, qo, thr, flags), ref, ql, thr)
+
+
 def test_hit_capacity_overflow_reruns(compact):
     wl, ref, dix = compact
     eng = cobs.Engine(dix, max_hits=4)
