@@ -159,28 +159,76 @@ __device__ __forceinline__ void unpack(const unsigned long long *src, uint32_t n
     }
 }
 
+// Ascending sort of one key per lane across a warp (bitonic network, 15
+// compare-exchange steps by shuffles); lanes without a key hold ~0.
+__device__ __forceinline__ unsigned long long warp_sort32(unsigned long long key) {
+    const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+    for (uint32_t k2 = 2; k2 <= 32; k2 <<= 1) {
+#pragma unroll
+        for (uint32_t j = k2 >> 1; j > 0; j >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, j);
+            const bool up = (lane & k2) == 0u;     // this lane's run ascends
+            const bool lower = (lane & j) == 0u;   // this lane is the lower of the pair
+            const unsigned long long lo = key < other ? key : other, hi = key < other ? other : key;
+            key = lower == up ? lo : hi;
+        }
+    }
+    return key;
+}
+
+constexpr uint32_t SORT_WARPS = SORT_THREADS / 32;
+constexpr uint32_t NO_QUERY = 0xFFFFFFFFu;
+
 // Queries with 1 to SORT_SMEM_KEYS hits (listed from the back of big_list by
-// k_hits_scan), a fixed grid looping over them: sort in shared memory.
+// k_hits_scan), a fixed grid looping over them, one listed query per warp and
+// round: up to 32 hits the warp sorts them in registers; larger lists are
+// sorted in shared memory by the whole CTA after the round's warp sorts.
 __global__ void __launch_bounds__(SORT_THREADS) k_hits_segsort(HitsArgs a) {
     __shared__ unsigned long long sA[SORT_SMEM_KEYS];
     __shared__ unsigned long long sB[SORT_SMEM_KEYS];
+    __shared__ uint32_t s_defer[SORT_WARPS];
     unsigned long long total = *a.hit_count;
     if (total > a.hit_cap) return;  // the host re-runs with a larger capacity
     const unsigned long long nmid = *a.mid_count;
-    for (unsigned long long k = blockIdx.x; k < nmid; k += gridDim.x) {
-        const uint32_t q = a.big_list[a.n_queries - 1u - (uint32_t)k];
-        const uint64_t o = a.hit_off[q];
-        const uint32_t n = (uint32_t)(a.hit_off[q + 1] - o);
-        __syncthreads();  // the previous query's keys are unpacked
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) sA[i] = a.keys[o + i];
-        __syncthreads();
-        unsigned long long *src = sA, *dst = sB;
-        for (uint32_t w = 1; w < n; w <<= 1) {
-            merge_pass(src, dst, n, w);
-            __syncthreads();
-            unsigned long long *t = src; src = dst; dst = t;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * SORT_WARPS; base < nmid;
+         base += (unsigned long long)gridDim.x * SORT_WARPS) {
+        const unsigned long long k = base + warp;
+        uint32_t defer = NO_QUERY;
+        if (k < nmid) {
+            const uint32_t q = a.big_list[a.n_queries - 1u - (uint32_t)k];
+            const uint64_t o = a.hit_off[q];
+            const uint32_t n = (uint32_t)(a.hit_off[q + 1] - o);
+            if (n <= 32u) {
+                const unsigned long long key = warp_sort32(lane < n ? a.keys[o + lane] : ~0ULL);
+                if (lane < n) {
+                    a.out_ids[o + lane] = (uint32_t)key;
+                    a.out_scores[o + lane] = ~(uint32_t)(key >> 32);
+                }
+            } else {
+                defer = q;
+            }
         }
-        unpack(src, n, o, a.out_ids, a.out_scores);
+        if (lane == 0) s_defer[warp] = defer;
+        __syncthreads();
+        for (uint32_t w = 0; w < SORT_WARPS; w++) {
+            const uint32_t q = s_defer[w];
+            if (q == NO_QUERY) continue;  // the same for every thread
+            const uint64_t o = a.hit_off[q];
+            const uint32_t n = (uint32_t)(a.hit_off[q + 1] - o);
+            for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) sA[i] = a.keys[o + i];
+            __syncthreads();
+            unsigned long long *src = sA, *dst = sB;
+            for (uint32_t wd = 1; wd < n; wd <<= 1) {
+                merge_pass(src, dst, n, wd);
+                __syncthreads();
+                unsigned long long *t = src; src = dst; dst = t;
+            }
+            unpack(src, n, o, a.out_ids, a.out_scores);
+            __syncthreads();  // sA and sB free for the next list
+        }
+        __syncthreads();  // every warp read s_defer before the next round writes it
     }
 }
 
